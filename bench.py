@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark: resistance distance by batched Lanczos iteration on one GB300.
+
+Workload: Chung-Lu power-law graph (n = 1,000,000 before the largest-component cut,
+exponent 2.1, mean degree 20, 1e7 endpoint draws, unweighted) with 256 uniform random
+(s,t) pairs answered in one batched query; FP32 vectors, FP64 alpha/beta/T_k; each pair
+stops when its estimated relative error is below 1e-7 (target: true relative error
+<= 1e-6, checked against the FP64 oracle on a sample of pairs).
+
+One step = one full query of the 256 pairs (every Lanczos step of every pair).
+value = pairs/s over all ranks with the pair ids already on the device; e2e = the same
+through the C ABI with host buffers (pinned pair ids in, host results out).
+
+``--impl reference`` times the CPU oracle (plain C, FP64, one pair per thread) on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RD (s,t) pairs/sec at rel.err<=1e-6 (batched Lanczos, Chung-Lu 1M, 256 pairs)"
+UNIT = "pairs/s"
+REL_TOL = 1e-7
+K_MAX = 200
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in ["spmm.cuh", "spmm_f32.cu"]:
+        h.update(open(os.path.join(ROOT, "paper_2601_11159_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def load_traffic():
+    """DRAM bytes per SpMM launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "spmm_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_sha1") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="rdclk", suffix=".csv")
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allmax(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(rank: int):
+    from graphgen import workloads as W
+
+    g, s, t = W.chunglu(1_000_000, 2.1, 20.0, 10_000_000, 256, W.BASE_SEED + 2 + 1000 * rank)
+    return g, s, t
+
+
+def cpu_oracle(g, s, t, sample: int):
+    from oracle import lanczos as O
+
+    O.build()
+    t0 = time.perf_counter()
+    r, k, used = O.lanczos_batch(g, s[:sample], t[:sample], k_max=K_MAX, stop_tol=1e-9, threads=0)
+    dt = time.perf_counter() - t0
+    return r, k, used, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    g, s, t = workload(0)
+    sample = args.ref_sample
+    times = []
+    for _ in range(args.warmup):
+        cpu_oracle(g, s, t, min(sample, 4))
+    used = 1
+    for _ in range(args.steps):
+        _, k, used, dt = cpu_oracle(g, s, t, sample)
+        times.append(dt)
+    total = sum(times)
+    value = sample * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "chunglu1m_256pairs", "n": g.n, "nnz": g.nnz, "pairs_per_step": sample,
+                   "sample": f"{sample} of the 256 pairs per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"{sample} pairs of the 256-pair workload per step, stop at relative "
+                                   f"increment 1e-9"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-sample", type=int, default=32)
+    ap.add_argument("--cpu-sample", type=int, default=32)
+    ap.add_argument("--plain-sample", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    import paper_2601_11159_gb300 as rd
+    from paper_2601_11159_gb300 import build as B
+
+    if not os.path.exists(B.LIB):
+        B.build()
+    g, s_np, t_np = workload(rank)
+    P = s_np.size
+    G = rd.Graph.from_csr(g)
+    s_dev = torch.from_numpy(s_np).cuda()
+    t_dev = torch.from_numpy(t_np).cuda()
+    opts = dict(mode="fp32", k_max=K_MAX, rel_tol=REL_TOL)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also settles the workspace)
+    for _ in range(args.warmup):
+        res = G.query(s_dev, t_dev, **opts)
+    torch.cuda.synchronize()
+
+    # device-resident timed region
+    clk = Clocks(local)
+    clk.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    spmm_ms = 0.0
+    spmm_n = 0
+    spmm_bytes = 0.0
+    steps_max = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = G.query(s_dev, t_dev, profile=True, **opts)
+        st = G.last_stats()
+        launches += st["launches"]
+        spmm_ms += st["spmm_ms"]
+        spmm_n += st["spmm_launches"]
+        spmm_bytes = st["spmm_bytes"]
+        steps_max = max(steps_max, st["steps"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = allmax(world, ms)
+    value = P * world * args.steps / (ms_max / 1000.0)
+    r_gpu = res.r.cpu().numpy()
+    iters = res.iters.cpu().numpy()
+    status = res.status.cpu().numpy()
+
+    # end to end: host (pinned) pair ids in, host results out, copies inside the timed region
+    s_h = torch.from_numpy(s_np).pin_memory()
+    t_h = torch.from_numpy(t_np).pin_memory()
+    for _ in range(2):
+        G.query(s_h, t_h, **opts)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        re2e = G.query(s_h, t_h, **opts)
+    torch.cuda.synchronize()
+    e2e_s = allmax(world, time.perf_counter() - t0)
+    e2e_value = P * world * args.steps / e2e_s
+    assert isinstance(re2e.r, np.ndarray)
+
+    # plain one-pair-per-launch path on a sample of the same pairs
+    ps = min(args.plain_sample, P)
+    for _ in range(2):
+        G.query(s_dev[:2], t_dev[:2], plain=True, **opts)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    rp = G.query(s_dev[:ps], t_dev[:ps], plain=True, **opts)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_value = ps / (p0.elapsed_time(p1) / 1000.0)
+    plain_r = rp.r.cpu().numpy()
+
+    if rank != 0:
+        return 0
+
+    peak, peak_kind = load_peaks()
+    avg_launch_ms = spmm_ms / max(spmm_n, 1)
+    achieved = spmm_bytes / (avg_launch_ms / 1000.0) / 1e9 if spmm_n else None
+    traffic = load_traffic()
+
+    cpu = None
+    max_rel = None
+    if not args.no_cpu:
+        cs = min(args.cpu_sample, P)
+        r_or, k_or, used, dt = cpu_oracle(g, s_np, t_np, cs)
+        rel = np.abs(r_gpu[:cs] - r_or) / np.abs(r_or)
+        rel_plain = np.abs(plain_r - r_or[:ps]) / np.abs(r_or[:ps])
+        max_rel = float(rel.max())
+        cpu = {"value": cs / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
+               "sample": f"{cs} of the 256 pairs, FP64 C Lanczos, stop at relative increment 1e-9",
+               "max_rel_err_gpu_vs_oracle": max_rel, "max_rel_err_plain_vs_oracle": float(rel_plain.max()),
+               "median_rel_err_gpu_vs_oracle": float(np.median(rel))}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "chunglu1m_256pairs", "n": g.n, "nnz": g.nnz, "pairs": P,
+                   "precision": "FP32 vectors and SpMM, FP64 alpha/beta/T_k and reductions",
+                   "stop": f"estimated relative error <= {REL_TOL}", "k_max": K_MAX,
+                   "lanczos_steps_max": int(steps_max), "iters_median": float(np.median(iters)),
+                   "rhs_tile": int(st["rhs_tile"]), "rows_per_warp": int(st["rows_per_warp"]),
+                   "l2": "inputs larger than L2 (two 1 GB vector blocks per query)",
+                   "parallelism": f"replicas x{world}, pairs sharded, no collective",
+                   "all_pairs_ok": bool(np.all(status >= 0))},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * 4 * P),
+                "d2h_bytes_per_step": int(24 * P)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "k_spmm (+ k_spmm_heavy)", "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "algorithmic_bytes_per_launch": spmm_bytes, "avg_launch_ms": avg_launch_ms},
+        "plain_pairs_per_s": plain_value,
+        "batched_over_plain": value / world / plain_value,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "max_rel_err": max_rel,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * rd.h -- resistance distance by Lanczos iteration on one GPU (sm_103a).
+ *
+ * C ABI of librd.so. Every call takes plain pointers and sizes; nothing here
+ * depends on PyTorch or any other framework.
+ *
+ * The method (paper: Section 3, Algorithm 3 and Eq. (approx_formula)): for an
+ * undirected connected graph with positive edge weights w_uv, degrees
+ * d_u = sum_v w_uv, Ahat = D^{-1/2} W D^{-1/2} and
+ * b = e_s/sqrt(d_s) - e_t/sqrt(d_t),
+ *
+ *     r(s,t) = (e_s - e_t)^T L^+ (e_s - e_t) = b^T (I - Ahat)^+ b
+ *           ~= ||b||^2 e_1^T (I - T_k)^{-1} e_1,
+ *
+ * with T_k the tridiagonal matrix built by k steps of the Lanczos three-term
+ * recurrence started from v_1 = b/||b|| (Eq. (lz_recurrence)). The
+ * resistance distance itself is the Definition of RD in Section 2.1.
+ *
+ * Conventions shared by all calls:
+ *  - Status: every call returns an rd_status; nothing throws across the ABI.
+ *    rd_last_error() returns a human-readable detail for the calling thread.
+ *  - Pointers marked "host or device" may be either; the library tells them
+ *    apart with cudaPointerGetAttributes and stages host buffers itself.
+ *    Device pointers must be device memory of the current CUDA device.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream). All device work of a call is ordered on that stream.
+ *    rd_query, rd_edge_grad and rd_potential synchronize that stream before
+ *    returning (they poll per-pair convergence), so their outputs are ready
+ *    on return.
+ *  - Ownership: the caller owns every pointer it passes. rd_graph owns only
+ *    what it allocates (its device copy of the CSR, derived arrays and a
+ *    grow-only workspace reused by later calls); rd_graph_destroy frees it.
+ *  - Threads: an rd_graph may be used by one thread at a time.
+ *  - Sizes: 1 <= n < 2^31, 0 <= nnz < 2^31.
+ */
+#ifndef RD_H
+#define RD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RD_ABI_VERSION 1
+
+typedef struct rd_graph rd_graph;
+
+typedef enum {
+    RD_OK = 0,
+    RD_WARN_NOT_CONVERGED = 1, /* per pair: k_max reached before the tolerance */
+    RD_ERR_INVALID_ARG = -1,   /* bad size, id out of range, bad CSR, NaN/negative weight */
+    RD_ERR_ZERO_DEGREE = -2,   /* a vertex has no incident edge (degree 0) */
+    RD_ERR_DISCONNECTED = -3,  /* per pair: s and t lie in different components (r = +inf) */
+    RD_ERR_CUDA = -4,          /* a CUDA runtime call failed */
+    RD_ERR_OOM = -5,           /* device allocation failed */
+    RD_ERR_TIMEOUT = -6,       /* a bounded device loop gave up */
+    RD_ERR_NUMERIC = -7,       /* per pair: I - T_k lost positive definiteness or a value is not finite */
+    RD_ERR_UNSUPPORTED = -8    /* valid request the library does not implement */
+} rd_status;
+
+typedef enum {
+    RD_MODE_FP64 = 0,        /* vectors, SpMV/SpMM and all scalars in FP64 */
+    RD_MODE_FP32V_FP64S = 1  /* vectors and SpMM in FP32; alpha, beta, T_k, its solve and every
+                                cross-thread reduction in FP64 */
+} rd_mode;
+
+/* rd_graph_create / rd_graph_set_weights flags */
+#define RD_INPUT_ON_DEVICE 1u   /* force: the CSR pointers are device pointers (else auto-detected) */
+#define RD_CHECK_SYMMETRY 2u    /* verify that (v,u,w) is stored for every (u,v,w); error if not */
+#define RD_LABEL_COMPONENTS 4u  /* label connected components so disconnected pairs get +inf */
+
+/* rd_query_opts.flags */
+#define RD_Q_FIXED_K 1u     /* ignore rel_tol/resid_tol: every pair runs exactly k_max steps
+                               (or stops at breakdown) */
+#define RD_Q_NO_DEFLATE 2u  /* do not remove the component along D^{1/2}1 from each new vector */
+#define RD_Q_PLAIN 4u       /* answer the pairs one at a time with the single-vector SpMV path */
+#define RD_Q_PROFILE 8u     /* time the dominant kernel with CUDA events (see rd_last_call_stats) */
+
+typedef struct {
+    int32_t k_max;         /* step cap (>= 1) */
+    double rel_tol;        /* stop when the estimated relative error of r is <= rel_tol (0 = off);
+                              estimate: the last 4 increments of e_1^T (I-T_k)^{-1} e_1 over its value */
+    double resid_tol;      /* stop when ||b - (I - Ahat) x_k|| / ||b|| <= resid_tol (0 = off) */
+    int32_t mode;          /* rd_mode */
+    int32_t rhs_tile;      /* right-hand-side columns per SpMM sweep; 0 = tuned */
+    int32_t rows_per_warp; /* rows a warp works on at once; 0 = tuned */
+    int32_t chunk_steps;   /* steps between host convergence polls; 0 = default (8) */
+    uint32_t flags;        /* RD_Q_* */
+} rd_query_opts;
+
+/* Per-call statistics of the last rd_query / rd_edge_grad / rd_potential on g. */
+typedef struct {
+    int64_t launches;        /* kernels this library launched during the call */
+    int64_t spmm_launches;   /* launches of the dominant SpMM/SpMV kernel */
+    double spmm_ms;          /* summed CUDA-event time of those launches (RD_Q_PROFILE only, else 0) */
+    int32_t steps;           /* Lanczos steps run (max over pairs) */
+    int32_t rhs_tile;        /* configuration used */
+    int32_t rows_per_warp;
+    int32_t nnz_lanes;       /* lanes that share one row's nonzeros */
+    int64_t ld;              /* padded number of right-hand-side columns (vector row stride) */
+    double spmm_bytes;       /* algorithmic bytes of one SpMM launch: 4*nnz (+4*nnz weights)
+                                + 8*(n+1) + 3*ld*n*sizeof(element) */
+} rd_call_stats;
+
+/* Fill `opts` with defaults: k_max 1000, rel_tol 1e-7, resid_tol 0, FP32 vectors with FP64
+ * scalars, tuned tiles, chunk 8, flags 0. */
+void rd_query_opts_init(rd_query_opts* opts);
+
+/* Build a device graph from symmetric CSR (Section 2.1: undirected graph; weighted
+ * generalisation as stated there).
+ *  n, nnz       : vertices and stored entries (each undirected edge is stored twice).
+ *  row_ptr      : int64[n+1], host or device, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *  col_idx      : int32[nnz], host or device, values in [0, n).
+ *  weights      : float[nnz] host or device, all > 0 and finite; NULL = unweighted (all 1).
+ *  flags        : RD_INPUT_ON_DEVICE | RD_CHECK_SYMMETRY | RD_LABEL_COMPONENTS.
+ * Self-loops are dropped (they cancel in L = D - W, so r is unchanged); duplicate entries
+ * are summed. The arrays are copied; the caller may free them after return.
+ * Errors: RD_ERR_INVALID_ARG (sizes, CSR shape, ids, weights, asymmetry when checked),
+ * RD_ERR_ZERO_DEGREE (a vertex with no edge, n > 1), RD_ERR_OOM, RD_ERR_CUDA.
+ * On error *out is NULL. */
+rd_status rd_graph_create(rd_graph** out, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                          const int32_t* col_idx, const float* weights, uint32_t flags, void* stream);
+
+/* Replace the edge weights (same structure, float[nnz] in the order given at create, before
+ * self-loop removal), host or device; recomputes degrees. Same weight errors as create. */
+rd_status rd_graph_set_weights(rd_graph* g, const float* weights, void* stream);
+
+/* Free everything the graph owns. NULL is accepted. */
+rd_status rd_graph_destroy(rd_graph* g);
+
+/* Host outputs (any may be NULL): vertices, stored entries after self-loop removal, whether
+ * weighted, number of components (0 if not labelled). */
+rd_status rd_graph_info(const rd_graph* g, int64_t* n, int64_t* nnz, int32_t* weighted,
+                        int32_t* ncomponents);
+
+/* Resistance distances of npairs (s,t) pairs (Algorithm 3, batched: all pairs advance
+ * together as one SpMM over an n x ld row-major block of vectors).
+ *  s, t           : int32[npairs], host or device, ids in [0, n).
+ *  opts           : NULL = rd_query_opts_init defaults.
+ *  r_out          : double[npairs], host or device: ||b||^2 e_1^T (I - T_k)^{-1} e_1.
+ *  iters_out      : int32[npairs] or NULL: k per pair.
+ *  err_est_out    : double[npairs] or NULL: estimated relative error (rel_tol's estimate).
+ *  pair_status_out: int32[npairs] or NULL: per-pair rd_status. s == t gives r = 0, RD_OK;
+ *                   different components (when labelled) give r = +inf, RD_ERR_DISCONNECTED;
+ *                   k_max reached gives the estimate so far and RD_WARN_NOT_CONVERGED;
+ *                   loss of definiteness gives the last good estimate and RD_ERR_NUMERIC.
+ * Per-pair problems do not fail the call. The call returns RD_OK, or RD_WARN_NOT_CONVERGED
+ * if any pair did not converge, or an error for the whole call (RD_ERR_INVALID_ARG for an
+ * id out of range or npairs < 0; RD_ERR_OOM; RD_ERR_CUDA). npairs == 0 returns RD_OK. */
+rd_status rd_query(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
+                   const rd_query_opts* opts, double* r_out, int32_t* iters_out, double* err_est_out,
+                   int32_t* pair_status_out, void* stream);
+
+/* Gradient of sum_p grad_r[p] * r(s_p, t_p) with respect to the stored edge weights.
+ * For stored entry e = (u -> v): grad_w_out[e] = 1/2 * sum_p grad_r[p] * dr_p/dw_uv with
+ * dr/dw_uv = -(phi(u) - phi(v))^2 and phi = sqrt(1/d_s+1/d_t) D^{-1/2} V_k (I-T_k)^{-1} e_1,
+ * the Lanczos potential of Section 6.3 (Algorithm 5, first line). Both stored copies of an
+ * edge get the same value, so moving both copies by delta changes the objective by
+ * delta * (sum of the two). phi is rebuilt by a second Lanczos pass that replays the
+ * stored alpha/beta (no basis V_k is kept).
+ *  grad_r     : double[npairs] host or device, or NULL for all ones.
+ *  grad_w_out : float[nnz_created] host or device (nnz as passed to create; entries that
+ *               were self-loops get 0).
+ *  r_out      : double[npairs] or NULL.
+ * Errors as rd_query. */
+rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
+                       const double* grad_r, const rd_query_opts* opts, float* grad_w_out,
+                       double* r_out, void* stream);
+
+/* Lanczos potentials (Section 6.3, Definition electric_flow and Algorithm 5, first line):
+ * phi_out is float[npairs][n] (pair-major), host or device; phi_p is defined up to an
+ * additive constant (the library's is orthogonal to the degree vector). Edge flows are
+ * f(e) = phi(u) - phi(v). r_out as rd_query (nullable). Errors as rd_query. */
+rd_status rd_potential(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
+                       const rd_query_opts* opts, float* phi_out, double* r_out, void* stream);
+
+/* Statistics of the last call on g (host struct). */
+rd_status rd_last_call_stats(const rd_graph* g, rd_call_stats* out);
+
+/* Static text for a status code. */
+const char* rd_status_string(rd_status s);
+
+/* Detail of the last error raised on the calling thread ("" if none). */
+const char* rd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RD_H */

@@ -1,0 +1,149 @@
+// Graph ingest kernels: CSR validation and degrees (Section 2.1: d_u = sum of the
+// weights of u's edges; Section 2.2: the D^{-1/2} scaling of Ahat, applied here as
+// 1/d_u per row because vectors are kept as q = D^{-1/2} v).
+#include <math.h>
+
+#include "rd_internal.cuh"
+
+namespace rd {
+
+struct CheckFlags {
+    int32_t bad_rowptr;
+    int32_t bad_col;
+    int32_t bad_weight;
+    int32_t zero_degree;
+    unsigned long long self_loops;
+};
+
+__global__ void k_check_csr(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* col, const float* w,
+                            CheckFlags* f)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t u = tid; u < n; u += stride) {
+        const int64_t a = rp[u], b = rp[u + 1];
+        if (a > b || a < 0 || b > nnz) atomicOr(&f->bad_rowptr, 1);
+    }
+    if (tid == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(&f->bad_rowptr, 1);
+    for (int64_t e = tid; e < nnz; e += stride) {
+        const int32_t c = col[e];
+        if (c < 0 || (int64_t)c >= n) atomicOr(&f->bad_col, 1);
+        if (w) {
+            const float x = w[e];
+            if (!(x > 0.0f) || !isfinite(x)) atomicOr(&f->bad_weight, 1);
+        }
+    }
+}
+
+// Self-loops need the row of each entry: one thread per row.
+__global__ void k_count_self_loops(int64_t n, const int64_t* rp, const int32_t* col, CheckFlags* f)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        unsigned long long c = 0;
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) c += (col[e] == (int32_t)u);
+        if (c) atomicAdd(&f->self_loops, c);
+    }
+}
+
+// Degrees in FP64 (fixed order along the row), derived FP32/FP64 copies, and
+// per-block partial sums of the degrees (summed on the host in block order).
+__global__ void k_degrees(int64_t n, const int64_t* rp, const float* w, double* deg64, double* invdeg64,
+                          float* deg32, float* invdeg32, double* block_sum, CheckFlags* f)
+{
+    __shared__ double red[256];
+    double local = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        double d = 0.0;
+        if (w) {
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e) d += (double)w[e];
+        } else {
+            d = (double)(rp[u + 1] - rp[u]);
+        }
+        deg64[u] = d;
+        invdeg64[u] = d > 0.0 ? 1.0 / d : 0.0;
+        deg32[u] = (float)d;
+        invdeg32[u] = d > 0.0 ? (float)(1.0 / d) : 0.0f;
+        if (!(d > 0.0)) atomicOr(&f->zero_degree, 1);
+        local += d;
+    }
+    red[threadIdx.x] = local;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_sum[blockIdx.x] = red[0];
+}
+
+static int grid_for(int64_t work, int sm)
+{
+    int64_t g = (work + 255) / 256;
+    const int64_t cap = (int64_t)sm * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+rd_status check_csr(rd_graph* g, cudaStream_t st, int64_t* self_loops)
+{
+    CheckFlags* f = nullptr;
+    RD_CUDA(cudaMallocAsync((void**)&f, sizeof(CheckFlags), st));
+    RD_CUDA(cudaMemsetAsync(f, 0, sizeof(CheckFlags), st));
+    k_check_csr<<<grid_for(g->nnz > g->n ? g->nnz : g->n, g->sm_count), 256, 0, st>>>(g->n, g->nnz, g->row_ptr,
+                                                                                       g->col, g->w, f);
+    CheckFlags h{};
+    RD_CUDA(cudaMemcpyAsync(&h, f, sizeof(CheckFlags), cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    if (h.bad_rowptr) {
+        cudaFreeAsync(f, st);
+        set_error("row_ptr must start at 0, be non-decreasing and end at nnz");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (h.bad_col) {
+        cudaFreeAsync(f, st);
+        set_error("a column index is outside [0, n)");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (h.bad_weight) {
+        cudaFreeAsync(f, st);
+        set_error("edge weights must be finite and > 0");
+        return RD_ERR_INVALID_ARG;
+    }
+    k_count_self_loops<<<grid_for(g->n, g->sm_count), 256, 0, st>>>(g->n, g->row_ptr, g->col, f);
+    RD_CUDA(cudaMemcpyAsync(&h, f, sizeof(CheckFlags), cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaFreeAsync(f, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    *self_loops = (int64_t)h.self_loops;
+    return RD_OK;
+}
+
+rd_status compute_degrees(rd_graph* g, cudaStream_t st)
+{
+    const int grid = grid_for(g->n, g->sm_count);
+    CheckFlags* f = nullptr;
+    double* bs = nullptr;
+    RD_CUDA(cudaMallocAsync((void**)&f, sizeof(CheckFlags), st));
+    RD_CUDA(cudaMallocAsync((void**)&bs, sizeof(double) * grid, st));
+    RD_CUDA(cudaMemsetAsync(f, 0, sizeof(CheckFlags), st));
+    k_degrees<<<grid, 256, 0, st>>>(g->n, g->row_ptr, g->w, g->deg64, g->invdeg64, g->deg32, g->invdeg32, bs, f);
+    CheckFlags h{};
+    std::vector<double> hb(grid);
+    RD_CUDA(cudaMemcpyAsync(&h, f, sizeof(CheckFlags), cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaMemcpyAsync(hb.data(), bs, sizeof(double) * grid, cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaFreeAsync(f, st));
+    RD_CUDA(cudaFreeAsync(bs, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (double x : hb) s += x;
+    g->sumdeg = s;
+    g->mean_deg = g->n ? s / (double)g->n : 0.0;
+    if (h.zero_degree && g->n > 1) {
+        set_error("a vertex has degree 0 (isolated vertex)");
+        return RD_ERR_ZERO_DEGREE;
+    }
+    return RD_OK;
+}
+
+}  // namespace rd

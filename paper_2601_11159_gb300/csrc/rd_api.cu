@@ -1,0 +1,1071 @@
+// C ABI of librd (declared in include/rd.h): graph ingest, batched Lanczos queries,
+// the recomputing adjoint for edge-weight gradients, and potentials.
+//
+// The driver runs Algorithm 3 (Section 3) for all pairs at once: per step an SpMM
+// (plus a pre-pass for heavy rows), an FP64 finalisation of alpha/beta and of the
+// running LDL^T factorisation of I - T_k, and a normalisation pass. The host polls
+// the number of active pairs every `chunk_steps` steps; kernels of steps after the
+// last active pair has stopped return at once.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "rd_internal.cuh"
+
+namespace rd {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+rd_status cuda_status(cudaError_t e, const char* what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    cudaGetLastError();  // clear a sticky-free error so later calls can proceed
+    return e == cudaErrorMemoryAllocation ? RD_ERR_OOM : RD_ERR_CUDA;
+}
+
+rd_status check_csr(rd_graph* g, cudaStream_t st, int64_t* self_loops);
+rd_status compute_degrees(rd_graph* g, cudaStream_t st);
+int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy);
+int spmm_blocks_per_sm_f64(const SpmmCfg& c, bool weighted, bool heavy);
+std::vector<SpmmCfg> spmm_configs_f32();
+std::vector<SpmmCfg> spmm_configs_f64();
+
+int spmm_blocks_per_sm(const SpmmCfg& c, bool weighted, bool heavy, bool fp64)
+{
+    return fp64 ? spmm_blocks_per_sm_f64(c, weighted, heavy) : spmm_blocks_per_sm_f32(c, weighted, heavy);
+}
+
+std::vector<SpmmCfg> spmm_configs(bool fp64) { return fp64 ? spmm_configs_f64() : spmm_configs_f32(); }
+
+static bool cfg_known(const SpmmCfg& c, bool fp64)
+{
+    for (const auto& x : spmm_configs(fp64))
+        if (x == c) return true;
+    return false;
+}
+
+// ------------------------------------------------------------- helpers
+static bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename X>
+    X* take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        X* p = reinterpret_cast<X*>(base ? base + off : nullptr);
+        off += sizeof(X) * (count ? count : 1);
+        return p;
+    }
+};
+
+static rd_status ensure_ws(rd_graph* g, size_t bytes)
+{
+    if (g->ws.bytes >= bytes) return RD_OK;
+    if (g->ws.base) {
+        cudaFree(g->ws.base);
+        g->ws.base = nullptr;
+        g->ws.bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("workspace allocation of " + std::to_string(bytes) + " bytes failed");
+        return RD_ERR_OOM;
+    }
+    g->ws.base = p;
+    g->ws.bytes = bytes;
+    return RD_OK;
+}
+
+// --------------------------------------------------------------- graph
+static void free_graph(rd_graph* g)
+{
+    if (!g) return;
+    void* ptrs[] = {g->row_ptr, g->col, g->w, g->keep_idx, g->deg64, g->invdeg64, g->deg32, g->invdeg32,
+                    g->comp, g->heavy_rows, g->heavy_first, g->chunk_beg, g->chunk_end, g->ws.base};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (g->h_pinned) cudaFreeHost(g->h_pinned);
+    delete g;
+}
+
+// Union-find over the CSR on the host (path halving, union by smaller root id);
+// labels are the root id of each vertex's component, made dense afterwards.
+static int32_t label_components(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& col,
+                                 std::vector<int32_t>& lab)
+{
+    std::vector<int32_t> par(n);
+    std::iota(par.begin(), par.end(), 0);
+    auto find = [&](int32_t x) {
+        while (par[x] != x) {
+            par[x] = par[par[x]];
+            x = par[x];
+        }
+        return x;
+    };
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+            int32_t a = find((int32_t)u), b = find(col[e]);
+            if (a != b) {
+                if (a < b) par[b] = a; else par[a] = b;
+            }
+        }
+    lab.assign(n, -1);
+    std::vector<int32_t> dense(n, -1);
+    int32_t nc = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        int32_t r = find((int32_t)u);
+        if (dense[r] < 0) dense[r] = nc++;
+        lab[u] = dense[r];
+    }
+    return nc;
+}
+
+static rd_status build_heavy(rd_graph* g, const std::vector<int64_t>& rp)
+{
+    std::vector<int32_t> rows, first, cb, ce;
+    first.push_back(0);
+    for (int64_t u = 0; u < g->n; ++u) {
+        const int64_t d = rp[u + 1] - rp[u];
+        if (d > g->heavy_thr) {
+            rows.push_back((int32_t)u);
+            for (int64_t e = rp[u]; e < rp[u + 1]; e += g->heavy_thr) {
+                cb.push_back((int32_t)e);
+                ce.push_back((int32_t)std::min<int64_t>(e + g->heavy_thr, rp[u + 1]));
+            }
+            first.push_back((int32_t)cb.size());
+        }
+    }
+    g->n_heavy_rows = (int64_t)rows.size();
+    g->n_chunks = (int64_t)cb.size();
+    if (g->n_heavy_rows == 0) return RD_OK;
+    RD_CUDA(cudaMalloc((void**)&g->heavy_rows, sizeof(int32_t) * rows.size()));
+    RD_CUDA(cudaMalloc((void**)&g->heavy_first, sizeof(int32_t) * first.size()));
+    RD_CUDA(cudaMalloc((void**)&g->chunk_beg, sizeof(int32_t) * cb.size()));
+    RD_CUDA(cudaMalloc((void**)&g->chunk_end, sizeof(int32_t) * ce.size()));
+    RD_CUDA(cudaMemcpy(g->heavy_rows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(g->heavy_first, first.data(), sizeof(int32_t) * first.size(), cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(g->chunk_beg, cb.data(), sizeof(int32_t) * cb.size(), cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(g->chunk_end, ce.data(), sizeof(int32_t) * ce.size(), cudaMemcpyHostToDevice));
+    return RD_OK;
+}
+
+static rd_status symmetric_check(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& col,
+                                 const std::vector<float>& w)
+{
+    struct E {
+        int64_t key;
+        float w;
+    };
+    const int64_t nnz = rp[n];
+    std::vector<E> fwd(nnz), bwd(nnz);
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+            const float x = w.empty() ? 1.0f : w[e];
+            fwd[e] = E{u * n + col[e], x};
+            bwd[e] = E{(int64_t)col[e] * n + u, x};
+        }
+    auto lt = [](const E& a, const E& b) { return a.key < b.key || (a.key == b.key && a.w < b.w); };
+    std::sort(fwd.begin(), fwd.end(), lt);
+    std::sort(bwd.begin(), bwd.end(), lt);
+    for (int64_t e = 0; e < nnz; ++e)
+        if (fwd[e].key != bwd[e].key || fwd[e].w != bwd[e].w) {
+            set_error("the CSR is not symmetric: entry (" + std::to_string(fwd[e].key / n) + ", " +
+                      std::to_string(fwd[e].key % n) + ") has no mirror with equal weight");
+            return RD_ERR_INVALID_ARG;
+        }
+    return RD_OK;
+}
+
+static rd_status graph_build(rd_graph* g, const int64_t* row_ptr, const int32_t* col_idx, const float* weights,
+                             uint32_t flags, cudaStream_t st)
+{
+    const int64_t n = g->n, nnz = g->nnz_in;
+    RD_CUDA(cudaMalloc((void**)&g->row_ptr, sizeof(int64_t) * (n + 1)));
+    RD_CUDA(cudaMalloc((void**)&g->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    if (weights) RD_CUDA(cudaMalloc((void**)&g->w, sizeof(float) * std::max<int64_t>(nnz, 1)));
+    RD_CUDA(cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDefault, st));
+    if (nnz) RD_CUDA(cudaMemcpyAsync(g->col, col_idx, sizeof(int32_t) * nnz, cudaMemcpyDefault, st));
+    if (weights && nnz) RD_CUDA(cudaMemcpyAsync(g->w, weights, sizeof(float) * nnz, cudaMemcpyDefault, st));
+    g->weighted = weights != nullptr;
+    g->nnz = nnz;
+    int64_t loops = 0;
+    RD_TRY(check_csr(g, st, &loops));
+
+    const bool need_full = loops > 0 || (flags & (RD_CHECK_SYMMETRY | RD_LABEL_COMPONENTS));
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> col;
+    std::vector<float> w;
+    RD_CUDA(cudaMemcpyAsync(rp.data(), g->row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    if (need_full) {
+        col.resize(nnz);
+        if (nnz) RD_CUDA(cudaMemcpyAsync(col.data(), g->col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st));
+        if (g->weighted) {
+            w.resize(nnz);
+            if (nnz) RD_CUDA(cudaMemcpyAsync(w.data(), g->w, sizeof(float) * nnz, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    RD_CUDA(cudaStreamSynchronize(st));
+
+    if (loops > 0) {  // drop self-loops (they cancel in L = D - W), keep the entry map
+        std::vector<int64_t> rp2(n + 1, 0), keep;
+        std::vector<int32_t> col2;
+        std::vector<float> w2;
+        keep.reserve(nnz - loops);
+        for (int64_t u = 0; u < n; ++u) {
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+                if (col[e] == (int32_t)u) continue;
+                keep.push_back(e);
+                col2.push_back(col[e]);
+                if (g->weighted) w2.push_back(w[e]);
+            }
+            rp2[u + 1] = (int64_t)col2.size();
+        }
+        rp.swap(rp2);
+        col.swap(col2);
+        w.swap(w2);
+        g->nnz = (int64_t)col.size();
+        RD_CUDA(cudaMalloc((void**)&g->keep_idx, sizeof(int64_t) * std::max<size_t>(keep.size(), 1)));
+        RD_CUDA(cudaMemcpy(g->row_ptr, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+        if (g->nnz) {
+            RD_CUDA(cudaMemcpy(g->keep_idx, keep.data(), sizeof(int64_t) * keep.size(), cudaMemcpyHostToDevice));
+            RD_CUDA(cudaMemcpy(g->col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice));
+            if (g->weighted) RD_CUDA(cudaMemcpy(g->w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    if (flags & RD_CHECK_SYMMETRY) RD_TRY(symmetric_check(n, rp, col, w));
+
+    RD_CUDA(cudaMalloc((void**)&g->deg64, sizeof(double) * n));
+    RD_CUDA(cudaMalloc((void**)&g->invdeg64, sizeof(double) * n));
+    RD_CUDA(cudaMalloc((void**)&g->deg32, sizeof(float) * n));
+    RD_CUDA(cudaMalloc((void**)&g->invdeg32, sizeof(float) * n));
+    RD_TRY(compute_degrees(g, st));
+    RD_TRY(build_heavy(g, rp));
+    if (flags & RD_LABEL_COMPONENTS) {
+        std::vector<int32_t> lab;
+        g->ncomp = label_components(n, rp, col, lab);
+        RD_CUDA(cudaMalloc((void**)&g->comp, sizeof(int32_t) * n));
+        RD_CUDA(cudaMemcpy(g->comp, lab.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    }
+    RD_CUDA(cudaMallocHost((void**)&g->h_pinned, 64));
+    return RD_OK;
+}
+
+// ------------------------------------------------------------- planning
+struct Plan {
+    bool fp64;
+    SpmmCfg cfg;
+    int64_t ld;
+    int grid_main, grid_heavy, grid_norm, nslab;
+    int k_max;
+    size_t elem;
+};
+
+static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bool fp64, bool plain)
+{
+    const double mdeg = g->n ? (double)g->nnz / (double)g->n : 0.0;
+    SpmmCfg c;
+    if (plain || P == 1) {
+        c.vec = 1;
+        c.gs = 1;
+        c.nzl = mdeg <= 6 ? 4 : (mdeg <= 12 ? 8 : (mdeg <= 24 ? 16 : 32));
+        if (o.rows_per_warp > 0) c.nzl = std::max(1, std::min(32, 32 / o.rows_per_warp));
+        return c;
+    }
+    int tp = o.rhs_tile;
+    if (tp <= 0) {
+        if (fp64) tp = P <= 8 ? 8 : (P <= 16 ? 16 : (P <= 32 ? 32 : 64));
+        else tp = P <= 16 ? 16 : (P <= 32 ? 32 : (P <= 64 ? 64 : 128));
+    }
+    c.vec = fp64 ? (tp >= 128 ? 4 : 2) : (tp >= 256 ? 8 : 4);
+    c.gs = std::max(1, tp / c.vec);
+    c.nzl = 1;
+    if (o.rows_per_warp > 0) c.nzl = std::max(1, 32 / (c.gs * o.rows_per_warp));
+    return c;
+}
+
+static rd_status make_plan(rd_graph* g, int64_t P, const rd_query_opts& o, bool plain, Plan* pl)
+{
+    pl->fp64 = o.mode == RD_MODE_FP64;
+    pl->elem = pl->fp64 ? 8 : 4;
+    pl->cfg = pick_cfg(g, P, o, pl->fp64, plain);
+    if (!cfg_known(pl->cfg, pl->fp64)) {
+        set_error("no SpMM kernel for rhs_tile/rows_per_warp = " + std::to_string(pl->cfg.tp()) + "/" +
+                  std::to_string(pl->cfg.rpw()));
+        return RD_ERR_UNSUPPORTED;
+    }
+    const int tp = pl->cfg.tp();
+    pl->ld = ((P + tp - 1) / tp) * tp;
+    pl->nslab = (int)(pl->ld / tp);
+    pl->k_max = o.k_max;
+    const int rows_per_block = kWarps * pl->cfg.rpw();
+    int bps = spmm_blocks_per_sm(pl->cfg, g->weighted, false, pl->fp64);
+    if (bps < 1) bps = 1;
+    int64_t gm = (int64_t)bps * g->sm_count;
+    gm = std::min<int64_t>(gm, (g->n + rows_per_block - 1) / rows_per_block);
+    pl->grid_main = (int)std::max<int64_t>(gm, 1);
+    int bph = spmm_blocks_per_sm(pl->cfg, g->weighted, true, pl->fp64);
+    if (bph < 1) bph = 1;
+    int64_t gh = (int64_t)bph * g->sm_count;
+    gh = std::min<int64_t>(gh, (g->n_chunks + rows_per_block - 1) / rows_per_block);
+    pl->grid_heavy = (int)std::max<int64_t>(gh, 1);
+    const int64_t units = (g->n * pl->ld) / (16 / (int64_t)pl->elem) + 1;
+    pl->grid_norm = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 8, (units + 255) / 256));
+    return RD_OK;
+}
+
+// ---------------------------------------------------------- workspace map
+struct Buffers {
+    void* q[2];
+    void* heavy_part;
+    double* block_part;
+    void* cf_hist;
+    PairState st;
+    int32_t* s;
+    int32_t* t;
+    double* r;
+    int32_t* iters;
+    double* err;
+    int32_t* status;
+    int32_t* summary;
+    int32_t* err_flag;
+    // gradient / potential
+    void* phi;
+    void* coef_hist;
+    void* gbar;
+    double* zscratch;
+    float* grad;
+    size_t state_bytes_begin, state_bytes_end;  // offsets of the region zeroed per query
+};
+
+static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, bool grad, Buffers* b)
+{
+    const int64_t ld = pl.ld, n = g->n, K = pl.k_max;
+    b->q[0] = c.take<char>(n * ld * pl.elem);
+    b->q[1] = c.take<char>(n * ld * pl.elem);
+    b->heavy_part = c.take<char>(std::max<int64_t>(g->n_chunks, 1) * ld * pl.elem);
+    b->block_part = c.take<double>((size_t)pl.nslab * pl.grid_main * 3 * pl.cfg.tp());
+    c.off = (c.off + 255) & ~size_t(255);
+    b->state_bytes_begin = c.off;
+    b->cf_hist = c.take<char>((K + 1) * 4 * ld * pl.elem);
+    PairState& s = b->st;
+    s.b2 = c.take<double>(ld);
+    s.delta = c.take<double>(ld);
+    s.g = c.take<double>(ld);
+    s.S = c.take<double>(ld);
+    s.beta = c.take<double>(ld);
+    s.ring = c.take<double>(kRing * ld);
+    s.r = c.take<double>(ld);
+    s.err = c.take<double>(ld);
+    s.resid = c.take<double>(ld);
+    s.k = c.take<int32_t>(ld);
+    s.status = c.take<int32_t>(ld);
+    s.active = c.take<int32_t>(ld);
+    s.hist_alpha = c.take<double>(K * ld);
+    s.hist_beta = c.take<double>((K + 1) * ld);
+    s.act_count = c.take<int32_t>(K + 2);
+    b->summary = c.take<int32_t>(2);
+    b->err_flag = c.take<int32_t>(1);
+    c.off = (c.off + 255) & ~size_t(255);
+    b->state_bytes_end = c.off;
+    b->s = c.take<int32_t>(P);
+    b->t = c.take<int32_t>(P);
+    b->r = c.take<double>(P);
+    b->iters = c.take<int32_t>(P);
+    b->err = c.take<double>(P);
+    b->status = c.take<int32_t>(P);
+    if (grad) {
+        b->phi = c.take<char>(n * ld * pl.elem);
+        b->coef_hist = c.take<char>(K * ld * pl.elem);
+        b->gbar = c.take<char>(ld * pl.elem);
+        b->zscratch = c.take<double>(K * 2 * ld);
+        b->grad = c.take<float>(std::max<int64_t>(g->nnz_in, 1));
+    } else {
+        b->phi = b->coef_hist = b->gbar = nullptr;
+        b->zscratch = nullptr;
+        b->grad = nullptr;
+    }
+    return c.off + 256;
+}
+
+struct EventPool {
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    cudaEvent_t get()
+    {
+        if (used == ev.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ev.push_back(e);
+        }
+        return ev[used++];
+    }
+    ~EventPool()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+// --------------------------------------------------------------- one run
+struct RunCtx {
+    rd_graph* g;
+    Plan pl;
+    Buffers b;
+    rd_query_opts o;
+    cudaStream_t st;
+    int64_t P;
+    int steps = 0;          // steps enqueued
+    int64_t launches = 0, spmm_launches = 0;
+    bool profile = false;
+    EventPool* ev = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
+};
+
+template <typename T>
+static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
+{
+    rd_graph* g = c.g;
+    StepArgs<T> a{};
+    a.n = g->n;
+    a.ld = c.pl.ld;
+    a.row_ptr = g->row_ptr;
+    a.col = g->col;
+    a.w = g->w;
+    if constexpr (sizeof(T) == 8) {
+        a.invdeg = g->invdeg64;
+        a.deg = g->deg64;
+    } else {
+        a.invdeg = g->invdeg32;
+        a.deg = g->deg32;
+    }
+    a.qcur = static_cast<const T*>(c.b.q[1]);
+    a.qprev_w = static_cast<T*>(c.b.q[0]);
+    a.cf_beta = static_cast<const T*>(c.b.cf_hist) + (int64_t)j * 4 * c.pl.ld;
+    a.heavy_thr = g->heavy_thr;
+    a.n_heavy_rows = g->n_heavy_rows;
+    a.n_chunks = g->n_chunks;
+    a.heavy_rows = g->heavy_rows;
+    a.heavy_first = g->heavy_first;
+    a.chunk_beg = g->chunk_beg;
+    a.chunk_end = g->chunk_end;
+    a.heavy_part = static_cast<T*>(c.b.heavy_part);
+    a.block_part = c.b.block_part;
+    a.active_prev = reduce ? c.b.st.act_count + j : nullptr;
+    a.do_reduce = reduce ? 1 : 0;
+    return a;
+}
+
+template <typename T>
+static rd_status enqueue_spmm(RunCtx& c, int j, bool reduce)
+{
+    StepArgs<T> a = step_args<T>(c, j, reduce);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c.profile) {
+        e0 = c.ev->get();
+        e1 = c.ev->get();
+        cudaEventRecord(e0, c.st);
+    }
+    const bool fp64 = sizeof(T) == 8;
+    if (c.g->n_chunks > 0) {
+        bool ok = fp64 ? launch_spmm_f64(c.pl.cfg, c.g->weighted, true, c.pl.grid_heavy, c.st,
+                                         *reinterpret_cast<StepArgs<double>*>(&a))
+                       : launch_spmm_f32(c.pl.cfg, c.g->weighted, true, c.pl.grid_heavy, c.st,
+                                         *reinterpret_cast<StepArgs<float>*>(&a));
+        if (!ok) return RD_ERR_UNSUPPORTED;
+        ++c.launches;
+    }
+    bool ok = fp64 ? launch_spmm_f64(c.pl.cfg, c.g->weighted, false, c.pl.grid_main, c.st,
+                                     *reinterpret_cast<StepArgs<double>*>(&a))
+                   : launch_spmm_f32(c.pl.cfg, c.g->weighted, false, c.pl.grid_main, c.st,
+                                     *reinterpret_cast<StepArgs<float>*>(&a));
+    if (!ok) return RD_ERR_UNSUPPORTED;
+    ++c.launches;
+    ++c.spmm_launches;
+    if (c.profile) {
+        cudaEventRecord(e1, c.st);
+        c.spmm_ev.emplace_back(e0, e1);
+    }
+    return RD_OK;
+}
+
+template <typename T>
+static void enqueue_normalize(RunCtx& c, int j, bool with_phi)
+{
+    NormArgs<T> a{};
+    a.n = c.g->n;
+    a.ld = c.pl.ld;
+    a.w_to_qnext = static_cast<T*>(c.b.q[0]);
+    a.qcur = static_cast<const T*>(c.b.q[1]);
+    a.cf = static_cast<const T*>(c.b.cf_hist) + (int64_t)j * 4 * c.pl.ld;
+    a.phi = with_phi ? static_cast<T*>(c.b.phi) : nullptr;
+    a.coef = with_phi ? static_cast<const T*>(c.b.coef_hist) + (int64_t)j * c.pl.ld : nullptr;
+    a.active_prev = with_phi ? nullptr : c.b.st.act_count + j;
+    if constexpr (sizeof(T) == 8) launch_normalize_f64(c.pl.grid_norm, c.st, a);
+    else launch_normalize_f32(c.pl.grid_norm, c.st, a);
+    ++c.launches;
+}
+
+static void enqueue_init(RunCtx& c, bool replay)
+{
+    const int64_t vbytes = c.g->n * c.pl.ld * (int64_t)c.pl.elem;
+    cudaMemsetAsync(c.b.q[0], 0, vbytes, c.st);
+    cudaMemsetAsync(c.b.q[1], 0, vbytes, c.st);
+    InitArgs a{};
+    a.n = c.g->n;
+    a.ld = c.pl.ld;
+    a.npairs = (int)c.P;
+    a.k_max = c.pl.k_max;
+    a.elem_size = (int)c.pl.elem;
+    a.s = c.b.s;
+    a.t = c.b.t;
+    a.deg64 = c.g->deg64;
+    a.comp = c.g->comp;
+    a.qcur = c.b.q[1];
+    a.err_flag = c.b.err_flag;
+    a.replay = replay ? 1 : 0;
+    a.st = c.b.st;
+    if (!replay) {
+        char* base = static_cast<char*>(c.g->ws.base);
+        cudaMemsetAsync(base + c.b.state_bytes_begin, 0, c.b.state_bytes_end - c.b.state_bytes_begin, c.st);
+    }
+    launch_init(c.st, a);
+    c.launches += 1;
+}
+
+template <typename T>
+static rd_status run_forward(RunCtx& c)
+{
+    enqueue_init(c, false);
+    const int chunk = c.o.chunk_steps > 0 ? c.o.chunk_steps : 8;
+    FinArgs fa{};
+    fa.ld = c.pl.ld;
+    fa.npairs = (int)c.P;
+    fa.tp = c.pl.cfg.tp();
+    fa.nblocks = c.pl.grid_main;
+    fa.k_max = c.pl.k_max;
+    fa.deflate = (c.o.flags & RD_Q_NO_DEFLATE) ? 0 : 1;
+    fa.fixed_k = (c.o.flags & RD_Q_FIXED_K) ? 1 : 0;
+    fa.fp64 = sizeof(T) == 8;
+    fa.rel_tol = c.o.rel_tol;
+    fa.resid_tol = c.o.resid_tol;
+    fa.sumdeg = c.g->sumdeg;
+    fa.block_part = c.b.block_part;
+    fa.st = c.b.st;
+    fa.cf_hist = c.b.cf_hist;
+    fa.elem_size = (int)c.pl.elem;
+    int* h = c.g->h_pinned;
+    // first poll: ids valid and at least one active pair
+    RD_CUDA(cudaMemcpyAsync(h, c.b.err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+    RD_CUDA(cudaMemcpyAsync(h + 1, c.b.st.act_count, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+    RD_CUDA(cudaStreamSynchronize(c.st));
+    if (h[0]) {
+        set_error("a pair id is outside [0, n)");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (h[1] == 0) return RD_OK;
+    for (int j = 0; j < c.pl.k_max; ++j) {
+        RD_TRY(enqueue_spmm<T>(c, j, true));
+        fa.step = j;
+        launch_finalize(c.st, fa);
+        ++c.launches;
+        enqueue_normalize<T>(c, j, false);
+        std::swap(c.b.q[0], c.b.q[1]);
+        c.steps = j + 1;
+        if ((j + 1) % chunk == 0 && j + 1 < c.pl.k_max) {
+            RD_CUDA(cudaMemcpyAsync(h, c.b.st.act_count + j + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+            RD_CUDA(cudaStreamSynchronize(c.st));
+            if (h[0] == 0) break;
+        }
+    }
+    RD_CUDA(cudaGetLastError());
+    return RD_OK;
+}
+
+static rd_status stage_pairs(RunCtx& c, const int32_t* s, const int32_t* t)
+{
+    RD_CUDA(cudaMemcpyAsync(c.b.s, s, sizeof(int32_t) * c.P, cudaMemcpyDefault, c.st));
+    RD_CUDA(cudaMemcpyAsync(c.b.t, t, sizeof(int32_t) * c.P, cudaMemcpyDefault, c.st));
+    return RD_OK;
+}
+
+static rd_status finish_outputs(RunCtx& c, double* r_out, int32_t* iters_out, double* err_out, int32_t* status_out,
+                                rd_status* call_status)
+{
+    OutArgs oa{};
+    oa.npairs = (int)c.P;
+    oa.ld = c.pl.ld;
+    oa.st = c.b.st;
+    oa.r_out = c.b.r;
+    oa.iters_out = c.b.iters;
+    oa.err_out = c.b.err;
+    oa.status_out = c.b.status;
+    oa.summary = c.b.summary;
+    launch_output(c.st, oa);
+    ++c.launches;
+    if (r_out) RD_CUDA(cudaMemcpyAsync(r_out, c.b.r, sizeof(double) * c.P, cudaMemcpyDefault, c.st));
+    if (iters_out) RD_CUDA(cudaMemcpyAsync(iters_out, c.b.iters, sizeof(int32_t) * c.P, cudaMemcpyDefault, c.st));
+    if (err_out) RD_CUDA(cudaMemcpyAsync(err_out, c.b.err, sizeof(double) * c.P, cudaMemcpyDefault, c.st));
+    if (status_out) RD_CUDA(cudaMemcpyAsync(status_out, c.b.status, sizeof(int32_t) * c.P, cudaMemcpyDefault, c.st));
+    int* h = c.g->h_pinned;
+    RD_CUDA(cudaMemcpyAsync(h, c.b.summary, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+    RD_CUDA(cudaStreamSynchronize(c.st));
+    RD_CUDA(cudaGetLastError());
+    *call_status = h[0] ? RD_WARN_NOT_CONVERGED : RD_OK;
+    return RD_OK;
+}
+
+static void record_stats(RunCtx& c)
+{
+    rd_call_stats& s = c.g->stats;
+    s.launches += c.launches;
+    s.spmm_launches += c.spmm_launches;
+    s.steps = std::max(s.steps, c.steps);
+    s.rhs_tile = c.pl.cfg.tp();
+    s.rows_per_warp = c.pl.cfg.rpw();
+    s.nnz_lanes = c.pl.cfg.nzl;
+    s.ld = c.pl.ld;
+    const double nnz = (double)c.g->nnz;
+    s.spmm_bytes = 4.0 * nnz + (c.g->weighted ? 4.0 * nnz : 0.0) + 8.0 * (double)(c.g->n + 1) +
+                   3.0 * (double)c.pl.ld * (double)c.g->n * (double)c.pl.elem;
+    if (c.profile) {
+        double ms = 0.0;
+        for (auto& pr : c.spmm_ev) {
+            float x = 0.f;
+            if (cudaEventElapsedTime(&x, pr.first, pr.second) == cudaSuccess) ms += x;
+        }
+        cudaGetLastError();
+        s.spmm_ms += ms;
+    }
+}
+
+static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
+                                 const rd_query_opts* opts, rd_query_opts* o)
+{
+    if (!g) {
+        set_error("graph is NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (npairs < 0 || npairs > (1ll << 24)) {
+        set_error("npairs must be in [0, 2^24]");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (npairs > 0 && (!s || !t)) {
+        set_error("s and t must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (opts) *o = *opts;
+    else rd_query_opts_init(o);
+    if (o->k_max < 1 || o->k_max > (1 << 22)) {
+        set_error("k_max must be in [1, 2^22]");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (o->mode != RD_MODE_FP64 && o->mode != RD_MODE_FP32V_FP64S) {
+        set_error("unknown mode");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (!(o->rel_tol >= 0.0) || !(o->resid_tol >= 0.0)) {
+        set_error("tolerances must be >= 0");
+        return RD_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device) {
+        cudaGetLastError();
+        set_error("the current CUDA device is not the graph's device");
+        return RD_ERR_INVALID_ARG;
+    }
+    return RD_OK;
+}
+
+static rd_status prepare_run(RunCtx& c, rd_graph* g, int64_t P, const rd_query_opts& o, bool plain, bool grad,
+                             cudaStream_t st)
+{
+    c.g = g;
+    c.o = o;
+    c.st = st;
+    c.P = P;
+    c.profile = (o.flags & RD_Q_PROFILE) != 0;
+    RD_TRY(make_plan(g, P, o, plain, &c.pl));
+    Carver dry(nullptr);
+    const size_t bytes = carve(dry, g, c.pl, P, grad, &c.b);
+    RD_TRY(ensure_ws(g, bytes));
+    Carver real(g->ws.base);
+    carve(real, g, c.pl, P, grad, &c.b);
+    return RD_OK;
+}
+
+// Host-side query of a batch of pairs (all device work on st).
+static rd_status query_batch(rd_graph* g, const int32_t* s, const int32_t* t, int64_t P, const rd_query_opts& o,
+                             bool plain, double* r_out, int32_t* iters_out, double* err_out, int32_t* status_out,
+                             cudaStream_t st, rd_status* call_status, EventPool* ev)
+{
+    RunCtx c;
+    c.ev = ev;
+    RD_TRY(prepare_run(c, g, P, o, plain, false, st));
+    RD_TRY(stage_pairs(c, s, t));
+    rd_status rs = o.mode == RD_MODE_FP64 ? run_forward<double>(c) : run_forward<float>(c);
+    if (rs < 0) return rs;
+    RD_TRY(finish_outputs(c, r_out, iters_out, err_out, status_out, call_status));
+    record_stats(c);
+    return RD_OK;
+}
+
+template <typename T>
+static rd_status run_replay(RunCtx& c, int K)
+{
+    // Replay of the forward recurrence with the stored coefficients; phi += coef_j q_j.
+    const int64_t vbytes = c.g->n * c.pl.ld * (int64_t)c.pl.elem;
+    RD_CUDA(cudaMemsetAsync(c.b.phi, 0, vbytes, c.st));
+    enqueue_init(c, true);
+    for (int j = 0; j < K; ++j) {
+        RD_TRY(enqueue_spmm<T>(c, j, false));
+        enqueue_normalize<T>(c, j, true);
+        std::swap(c.b.q[0], c.b.q[1]);
+    }
+    RD_CUDA(cudaGetLastError());
+    return RD_OK;
+}
+
+static rd_status forward_and_potential(RunCtx& c, const int32_t* s, const int32_t* t, const double* grad_r,
+                                       rd_status* call_status)
+{
+    RD_TRY(stage_pairs(c, s, t));
+    rd_status rs = c.pl.fp64 ? run_forward<double>(c) : run_forward<float>(c);
+    if (rs < 0) return rs;
+    // z-solve and gbar; a host grad_r is staged in the output buffer (free until the end)
+    const double* d_grad = nullptr;
+    if (grad_r) {
+        if (is_device_ptr(grad_r)) {
+            d_grad = grad_r;
+        } else {
+            RD_CUDA(cudaMemcpyAsync(c.b.r, grad_r, sizeof(double) * c.P, cudaMemcpyHostToDevice, c.st));
+            d_grad = c.b.r;
+        }
+    }
+    ZsolveArgs za{};
+    za.npairs = (int)c.P;
+    za.ld = c.pl.ld;
+    za.k_max = c.pl.k_max;
+    za.st = c.b.st;
+    za.coef_hist = c.b.coef_hist;
+    za.gbar = c.b.gbar;
+    za.zscratch = c.b.zscratch;
+    za.elem_size = (int)c.pl.elem;
+    za.grad_r = d_grad;
+    launch_zsolve(c.st, za);
+    ++c.launches;
+    // K = max steps over pairs
+    std::vector<int32_t> ks(c.P);
+    RD_CUDA(cudaMemcpyAsync(ks.data(), c.b.st.k, sizeof(int32_t) * c.P, cudaMemcpyDeviceToHost, c.st));
+    RD_CUDA(cudaStreamSynchronize(c.st));
+    int K = 0;
+    for (int32_t k : ks) K = std::max(K, (int)k);
+    rs = c.pl.fp64 ? run_replay<double>(c, K) : run_replay<float>(c, K);
+    if (rs < 0) return rs;
+    *call_status = RD_OK;
+    return RD_OK;
+}
+
+}  // namespace rd
+
+using namespace rd;
+
+// =================================================================== C ABI
+extern "C" {
+
+void rd_query_opts_init(rd_query_opts* o)
+{
+    if (!o) return;
+    o->k_max = 1000;
+    o->rel_tol = 1e-7;
+    o->resid_tol = 0.0;
+    o->mode = RD_MODE_FP32V_FP64S;
+    o->rhs_tile = 0;
+    o->rows_per_warp = 0;
+    o->chunk_steps = 8;
+    o->flags = 0;
+}
+
+const char* rd_status_string(rd_status s)
+{
+    switch (s) {
+        case RD_OK: return "ok";
+        case RD_WARN_NOT_CONVERGED: return "not converged within k_max";
+        case RD_ERR_INVALID_ARG: return "invalid argument";
+        case RD_ERR_ZERO_DEGREE: return "vertex of degree zero";
+        case RD_ERR_DISCONNECTED: return "s and t are disconnected";
+        case RD_ERR_CUDA: return "CUDA error";
+        case RD_ERR_OOM: return "out of device memory";
+        case RD_ERR_TIMEOUT: return "timeout";
+        case RD_ERR_NUMERIC: return "numerical breakdown";
+        case RD_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* rd_last_error(void) { return g_last_error.c_str(); }
+
+rd_status rd_graph_create(rd_graph** out, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                          const float* weights, uint32_t flags, void* stream)
+{
+    g_last_error.clear();
+    if (!out) {
+        set_error("out is NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (n < 1 || n >= (1ll << 31) || nnz < 0 || nnz >= (1ll << 31)) {
+        set_error("need 1 <= n < 2^31 and 0 <= nnz < 2^31");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (!row_ptr || (nnz > 0 && !col_idx)) {
+        set_error("row_ptr/col_idx must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    rd_graph* g = new rd_graph();
+    g->n = n;
+    g->nnz_in = nnz;
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+        rd_status s = cuda_status(cudaGetLastError(), "cudaGetDevice");
+        delete g;
+        return s == RD_OK ? RD_ERR_CUDA : s;
+    }
+    rd_status s = graph_build(g, row_ptr, col_idx, weights, flags, static_cast<cudaStream_t>(stream));
+    if (s < 0) {
+        free_graph(g);
+        return s;
+    }
+    *out = g;
+    return RD_OK;
+}
+
+rd_status rd_graph_set_weights(rd_graph* g, const float* weights, void* stream)
+{
+    g_last_error.clear();
+    if (!g || !weights) {
+        set_error("graph and weights must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!g->w) RD_CUDA(cudaMalloc((void**)&g->w, sizeof(float) * std::max<int64_t>(g->nnz_in, 1)));
+    if (g->keep_idx) {
+        std::vector<float> win(g->nnz_in), wk(g->nnz);
+        std::vector<int64_t> keep(g->nnz);
+        RD_CUDA(cudaMemcpyAsync(win.data(), weights, sizeof(float) * g->nnz_in, cudaMemcpyDefault, st));
+        RD_CUDA(cudaMemcpyAsync(keep.data(), g->keep_idx, sizeof(int64_t) * g->nnz, cudaMemcpyDeviceToHost, st));
+        RD_CUDA(cudaStreamSynchronize(st));
+        for (int64_t e = 0; e < g->nnz; ++e) wk[e] = win[keep[e]];
+        RD_CUDA(cudaMemcpy(g->w, wk.data(), sizeof(float) * g->nnz, cudaMemcpyHostToDevice));
+    } else if (g->nnz) {
+        RD_CUDA(cudaMemcpyAsync(g->w, weights, sizeof(float) * g->nnz, cudaMemcpyDefault, st));
+    }
+    g->weighted = true;
+    int64_t loops = 0;
+    RD_TRY(check_csr(g, st, &loops));
+    return compute_degrees(g, st);
+}
+
+rd_status rd_graph_destroy(rd_graph* g)
+{
+    free_graph(g);
+    return RD_OK;
+}
+
+rd_status rd_graph_info(const rd_graph* g, int64_t* n, int64_t* nnz, int32_t* weighted, int32_t* ncomponents)
+{
+    if (!g) {
+        set_error("graph is NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (weighted) *weighted = g->weighted ? 1 : 0;
+    if (ncomponents) *ncomponents = g->ncomp;
+    return RD_OK;
+}
+
+rd_status rd_last_call_stats(const rd_graph* g, rd_call_stats* out)
+{
+    if (!g || !out) {
+        set_error("graph and out must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    *out = g->stats;
+    return RD_OK;
+}
+
+rd_status rd_query(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs, const rd_query_opts* opts,
+                   double* r_out, int32_t* iters_out, double* err_est_out, int32_t* pair_status_out, void* stream)
+{
+    g_last_error.clear();
+    rd_query_opts o;
+    RD_TRY(validate_common(g, s, t, npairs, opts, &o));
+    if (npairs > 0 && !r_out) {
+        set_error("r_out must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    g->stats = rd_call_stats{};
+    if (npairs == 0) return RD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EventPool ev;
+    rd_status call = RD_OK;
+    if (o.flags & RD_Q_PLAIN) {
+        // one pair per run through the single-vector SpMV path
+        for (int64_t p = 0; p < npairs; ++p) {
+            rd_status one = RD_OK;
+            RD_TRY(query_batch(g, s + p, t + p, 1, o, true, r_out + p, iters_out ? iters_out + p : nullptr,
+                               err_est_out ? err_est_out + p : nullptr,
+                               pair_status_out ? pair_status_out + p : nullptr, st, &one, &ev));
+            if (one == RD_WARN_NOT_CONVERGED) call = one;
+        }
+        return call;
+    }
+    RD_TRY(query_batch(g, s, t, npairs, o, false, r_out, iters_out, err_est_out, pair_status_out, st, &call, &ev));
+    return call;
+}
+
+rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs, const double* grad_r,
+                       const rd_query_opts* opts, float* grad_w_out, double* r_out, void* stream)
+{
+    g_last_error.clear();
+    rd_query_opts o;
+    RD_TRY(validate_common(g, s, t, npairs, opts, &o));
+    if (!grad_w_out && g->nnz_in > 0) {
+        set_error("grad_w_out must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    g->stats = rd_call_stats{};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (npairs == 0) {
+        if (g->nnz_in) RD_CUDA(cudaMemsetAsync(grad_w_out, 0, sizeof(float) * g->nnz_in, st));
+        RD_CUDA(cudaStreamSynchronize(st));
+        return RD_OK;
+    }
+    EventPool ev;
+    RunCtx c;
+    c.ev = &ev;
+    RD_TRY(prepare_run(c, g, npairs, o, false, true, st));
+    rd_status call = RD_OK;
+    RD_TRY(forward_and_potential(c, s, t, grad_r, &call));
+    // edge kernel over internal entries, then map to the caller's entry order
+    const int grid = std::max(1, std::min(g->sm_count * 8, (int)((g->n + 7) / 8)));
+    float* gint = c.b.grad;
+    if (c.pl.fp64) {
+        EdgeGradArgs<double> a{};
+        a.n = g->n;
+        a.ld = c.pl.ld;
+        a.npairs = (int)npairs;
+        a.row_ptr = g->row_ptr;
+        a.col = g->col;
+        a.phi = static_cast<const double*>(c.b.phi);
+        a.gbar = static_cast<const double*>(c.b.gbar);
+        a.grad_out = gint;
+        launch_edge_grad_f64(grid, st, a);
+    } else {
+        EdgeGradArgs<float> a{};
+        a.n = g->n;
+        a.ld = c.pl.ld;
+        a.npairs = (int)npairs;
+        a.row_ptr = g->row_ptr;
+        a.col = g->col;
+        a.phi = static_cast<const float*>(c.b.phi);
+        a.gbar = static_cast<const float*>(c.b.gbar);
+        a.grad_out = gint;
+        launch_edge_grad_f32(grid, st, a);
+    }
+    ++c.launches;
+    if (g->keep_idx) {
+        std::vector<float> gi(g->nnz), go(g->nnz_in, 0.0f);
+        std::vector<int64_t> keep(g->nnz);
+        RD_CUDA(cudaMemcpyAsync(gi.data(), gint, sizeof(float) * g->nnz, cudaMemcpyDeviceToHost, st));
+        RD_CUDA(cudaMemcpyAsync(keep.data(), g->keep_idx, sizeof(int64_t) * g->nnz, cudaMemcpyDeviceToHost, st));
+        RD_CUDA(cudaStreamSynchronize(st));
+        for (int64_t e = 0; e < g->nnz; ++e) go[keep[e]] = gi[e];
+        RD_CUDA(cudaMemcpyAsync(grad_w_out, go.data(), sizeof(float) * g->nnz_in, cudaMemcpyDefault, st));
+        RD_CUDA(cudaStreamSynchronize(st));
+    } else if (g->nnz) {
+        RD_CUDA(cudaMemcpyAsync(grad_w_out, gint, sizeof(float) * g->nnz, cudaMemcpyDefault, st));
+    }
+    rd_status outs = RD_OK;
+    RD_TRY(finish_outputs(c, r_out, nullptr, nullptr, nullptr, &outs));
+    record_stats(c);
+    return outs;
+}
+
+}  // extern "C"
+
+namespace rd {
+template <typename T>
+__global__ void k_phi_out(int64_t n, int64_t ld, int npairs, const T* phi, float* out)
+{
+    const int64_t total = n * (int64_t)npairs;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int64_t p = i / n, u = i % n;
+        out[i] = (float)phi[u * ld + p];
+    }
+}
+}  // namespace rd
+
+extern "C" rd_status rd_potential(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
+                                  const rd_query_opts* opts, float* phi_out, double* r_out, void* stream)
+{
+    g_last_error.clear();
+    rd_query_opts o;
+    RD_TRY(validate_common(g, s, t, npairs, opts, &o));
+    if (npairs > 0 && !phi_out) {
+        set_error("phi_out must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    g->stats = rd_call_stats{};
+    if (npairs == 0) return RD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EventPool ev;
+    RunCtx c;
+    c.ev = &ev;
+    RD_TRY(prepare_run(c, g, npairs, o, false, true, st));
+    rd_status call = RD_OK;
+    RD_TRY(forward_and_potential(c, s, t, nullptr, &call));
+    // phi (n x ld, q-space) -> pair-major float output
+    float* stage = nullptr;
+    const bool dev_out = is_device_ptr(phi_out);
+    const size_t bytes = sizeof(float) * (size_t)g->n * (size_t)npairs;
+    if (dev_out) {
+        stage = phi_out;
+    } else {
+        RD_CUDA(cudaMallocAsync((void**)&stage, bytes, st));
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g->sm_count * 8, (g->n * npairs + 255) / 256));
+    if (c.pl.fp64) k_phi_out<double><<<grid, 256, 0, st>>>(g->n, c.pl.ld, (int)npairs, static_cast<double*>(c.b.phi), stage);
+    else k_phi_out<float><<<grid, 256, 0, st>>>(g->n, c.pl.ld, (int)npairs, static_cast<float*>(c.b.phi), stage);
+    ++c.launches;
+    if (!dev_out) {
+        RD_CUDA(cudaMemcpyAsync(phi_out, stage, bytes, cudaMemcpyDeviceToHost, st));
+        RD_CUDA(cudaFreeAsync(stage, st));
+    }
+    rd_status outs = RD_OK;
+    RD_TRY(finish_outputs(c, r_out, nullptr, nullptr, nullptr, &outs));
+    record_stats(c);
+    return outs;
+}

@@ -1,0 +1,220 @@
+// Internal declarations of librd: graph object, workspace, kernel argument
+// blocks and the launcher table. Not part of the public ABI (see include/rd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rd.h"
+
+namespace rd {
+
+// ----------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+rd_status cuda_status(cudaError_t e, const char* what);
+
+#define RD_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::rd::cuda_status(_e, #call);     \
+    } while (0)
+
+#define RD_TRY(call)                                                    \
+    do {                                                                \
+        rd_status _s = (call);                                          \
+        if (_s < 0) return _s;                                          \
+    } while (0)
+
+// ------------------------------------------------------- SpMM configuration
+// One warp is split into row groups of GS*NZL lanes. GS lanes span the
+// right-hand-side tile (VEC elements each, so the tile is TP = VEC*GS
+// columns); NZL lanes share the nonzeros of one row; RPW = 32/(GS*NZL) rows
+// are in flight per warp.
+struct SpmmCfg {
+    int vec = 4, gs = 32, nzl = 1;
+    int tp() const { return vec * gs; }
+    int rpw() const { return 32 / (gs * nzl); }
+    bool operator==(const SpmmCfg& o) const { return vec == o.vec && gs == o.gs && nzl == o.nzl; }
+};
+
+constexpr int kBlock = 256;        // threads per block of the SpMM kernels
+constexpr int kWarps = kBlock / 32;
+constexpr int kRing = 4;           // increments kept for the delayed error estimate
+
+// Argument block of one Lanczos step's SpMM (q-space: q = D^{-1/2} v).
+template <typename T>
+struct StepArgs {
+    int64_t n, ld;                 // rows, padded columns (row stride of vector blocks)
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* w;                // nullable (unweighted)
+    const T* invdeg;               // 1/d_u
+    const T* deg;                  // d_u
+    const T* qcur;                 // q_i  (n x ld)
+    T* qprev_w;                    // in: q_{i-1}; out: W = D^{-1} W_adj q_i - beta_i q_{i-1}
+    const T* cf_beta;              // beta_i per column (ld)
+    // heavy rows (degree > heavy_thr): chunk partial sums made by the heavy kernel
+    int heavy_thr;
+    int64_t n_heavy_rows, n_chunks;
+    const int32_t* heavy_rows;     // sorted row ids
+    const int32_t* heavy_first;    // n_heavy_rows + 1 chunk offsets
+    const int32_t* chunk_beg;      // nnz range of each chunk
+    const int32_t* chunk_end;
+    T* heavy_part;                 // n_chunks x ld
+    double* block_part;            // [slab][block][3][TP]
+    const int32_t* active_prev;    // early exit when *active_prev == 0 (nullable)
+    int do_reduce;
+};
+
+template <typename T>
+struct NormArgs {
+    int64_t n, ld;
+    T* w_to_qnext;                 // in: W, out: q_{i+1} (in place)
+    const T* qcur;
+    const T* cf;                   // [4][ld]: beta_i, alpha_i, c_i, 1/beta_{i+1}
+    T* phi;                        // nullable: phi += coef * q_i (replay pass)
+    const T* coef;                 // ld, with phi
+    const int32_t* active_prev;
+};
+
+// Per-pair FP64 state of the running LDL^T factorisation of I - T_k.
+struct PairState {
+    double* b2;        // ||b||^2 = 1/d_s + 1/d_t
+    double* delta;     // last pivot
+    double* g;         // last entry of L^{-1} e_1
+    double* S;         // e_1^T (I - T_k)^{-1} e_1
+    double* beta;      // beta_{k+1}
+    double* ring;      // kRing x ld increments
+    double* r;         // b2 * S
+    double* err;       // estimated relative error
+    double* resid;     // relative residual
+    int32_t* k;        // steps done
+    int32_t* status;   // rd_status per pair
+    int32_t* active;   // 1 while iterating
+    double* hist_alpha;   // k_max x ld
+    double* hist_beta;    // (k_max + 1) x ld: beta_1 .. beta_{k_max+1}
+    int32_t* act_count;   // k_max + 1 counters: active pairs entering step j
+};
+
+struct FinArgs {
+    int64_t ld;
+    int npairs, tp, nblocks, step;      // step: 0-based index of the step just reduced
+    int k_max, deflate, fixed_k, fp64;
+    double rel_tol, resid_tol, sumdeg;
+    const double* block_part;
+    PairState st;
+    void* cf_hist;                      // T [k_max+1][4][ld]
+    int elem_size;
+};
+
+// --------------------------------------------------------------- graph
+struct Workspace {
+    void* base = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace rd
+
+struct rd_graph {
+    int device = 0, sm_count = 0;
+    int64_t n = 0, nnz = 0, nnz_in = 0;
+    bool weighted = false;
+    int64_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    float* w = nullptr;
+    int64_t* keep_idx = nullptr;      // internal entry -> original entry (only if self-loops dropped)
+    double* deg64 = nullptr;
+    double* invdeg64 = nullptr;
+    float* deg32 = nullptr;
+    float* invdeg32 = nullptr;
+    double sumdeg = 0.0;
+    int32_t* comp = nullptr;
+    int32_t ncomp = 0;
+    // heavy-row chunks
+    int heavy_thr = 256;
+    int64_t n_heavy_rows = 0, n_chunks = 0;
+    int32_t* heavy_rows = nullptr;
+    int32_t* heavy_first = nullptr;
+    int32_t* chunk_beg = nullptr;
+    int32_t* chunk_end = nullptr;
+    double mean_deg = 0.0;
+    rd::Workspace ws;
+    rd_call_stats stats{};
+    int* h_pinned = nullptr;          // small pinned host buffer for polls
+};
+
+namespace rd {
+
+// Launchers (defined in the kernel translation units).
+// Returns false if the configuration is not instantiated.
+bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
+                     const StepArgs<float>& a);
+bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
+                     const StepArgs<double>& a);
+int spmm_blocks_per_sm(const SpmmCfg& c, bool weighted, bool heavy, bool fp64);
+std::vector<SpmmCfg> spmm_configs(bool fp64);
+
+void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a);
+void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a);
+void launch_finalize(cudaStream_t st, const FinArgs& a);
+
+struct InitArgs {
+    int64_t n, ld;
+    int npairs, k_max, elem_size;
+    const int32_t* s;
+    const int32_t* t;
+    const double* deg64;
+    const int32_t* comp;          // nullable
+    void* qcur;                   // T n x ld (zeroed before)
+    PairState st;
+    int32_t* err_flag;
+    int replay;                   // 1: only rebuild q_1 (the per-pair state is left untouched)
+};
+void launch_init(cudaStream_t st, const InitArgs& a);
+
+struct OutArgs {
+    int npairs;
+    int64_t ld;
+    PairState st;
+    double* r_out;
+    int32_t* iters_out;
+    double* err_out;
+    int32_t* status_out;
+    int32_t* summary;            // [0]: any not converged, [1]: any numeric
+};
+void launch_output(cudaStream_t st, const OutArgs& a);
+
+struct ZsolveArgs {
+    int npairs;
+    int64_t ld;
+    int k_max;
+    PairState st;
+    const double* grad_r;         // nullable (ones)
+    void* coef_hist;              // T [k_max][ld]: sqrt(b2) * z_j (0 beyond k_p)
+    void* gbar;                   // T [ld]: upstream gradient per column (0 if unused)
+    double* zscratch;             // [k_max][2][ld]
+    int elem_size;
+};
+void launch_zsolve(cudaStream_t st, const ZsolveArgs& a);
+
+template <typename T>
+struct EdgeGradArgs {
+    int64_t n, ld;
+    int npairs;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const T* phi;                 // n x ld
+    const T* gbar;                // ld
+    float* grad_out;              // internal entries
+};
+void launch_edge_grad_f32(int grid, cudaStream_t st, const EdgeGradArgs<float>& a);
+void launch_edge_grad_f64(int grid, cudaStream_t st, const EdgeGradArgs<double>& a);
+
+// Graph preparation kernels.
+rd_status graph_prepare(rd_graph* g, cudaStream_t st, uint32_t flags);
+rd_status graph_weights_changed(rd_graph* g, cudaStream_t st);
+
+}  // namespace rd

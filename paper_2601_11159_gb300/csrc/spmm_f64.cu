@@ -1,0 +1,45 @@
+// FP64 instantiations of the SpMM step (FP64 vectors and sums).
+#include "spmm.cuh"
+
+namespace rd {
+
+#define RD_F64_CONFIGS(X) \
+    X(1, 1, 4)            \
+    X(1, 1, 8)            \
+    X(1, 1, 16)           \
+    X(1, 1, 32)           \
+    X(2, 4, 1)            \
+    X(2, 8, 1)            \
+    X(2, 16, 1)           \
+    X(2, 32, 1)           \
+    X(4, 32, 1)
+
+bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
+                     const StepArgs<double>& a)
+{
+#define X(V, G, Z) \
+    if (c.vec == V && c.gs == G && c.nzl == Z) return launch_cfg<double, V, G, Z>(weighted, heavy, grid, st, a);
+    RD_F64_CONFIGS(X)
+#undef X
+    return false;
+}
+
+int spmm_blocks_per_sm_f64(const SpmmCfg& c, bool weighted, bool heavy)
+{
+#define X(V, G, Z) \
+    if (c.vec == V && c.gs == G && c.nzl == Z) return occupancy_cfg<double, V, G, Z>(weighted, heavy);
+    RD_F64_CONFIGS(X)
+#undef X
+    return 0;
+}
+
+std::vector<SpmmCfg> spmm_configs_f64()
+{
+    std::vector<SpmmCfg> v;
+#define X(V, G, Z) v.push_back(SpmmCfg{V, G, Z});
+    RD_F64_CONFIGS(X)
+#undef X
+    return v;
+}
+
+}  // namespace rd

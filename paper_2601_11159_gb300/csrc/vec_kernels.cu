@@ -1,0 +1,386 @@
+// Per-step vector and per-pair scalar kernels of the batched Lanczos iteration:
+// start vector (Algorithm 3, first line), FP64 finalisation of alpha/beta with an
+// O(1)-per-step LDL^T update of I - T_k (Eq. (approx_formula)), normalisation
+// (line "v_{i+1} = v_{i+1}/beta_{i+1}"), output, the tridiagonal solve for the
+// potential (Algorithm 5, first line) and the edge-weight gradient.
+#include <math.h>
+
+#include "spmm.cuh"
+
+namespace rd {
+
+// ----------------------------------------------------------------- start
+// q_1 = D^{-1/2} v_1 with v_1 = (e_s/sqrt(d_s) - e_t/sqrt(d_t)) / ||b||, so
+// q_1[s] = 1/(d_s ||b||), q_1[t] = -1/(d_t ||b||); ||b||^2 = 1/d_s + 1/d_t.
+template <typename T>
+__global__ void k_init(const InitArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs) return;
+    const PairState& st = a.st;
+    const int32_t s = a.s[p], t = a.t[p];
+    if (a.replay) {
+        if (st.status[p] == RD_OK || st.status[p] == RD_WARN_NOT_CONVERGED) {
+            if (s != t && st.b2[p] > 0.0) {
+                const double ds = a.deg64[s], dt = a.deg64[t];
+                const double bn = sqrt(1.0 / ds + 1.0 / dt);
+                T* q = static_cast<T*>(a.qcur);
+                q[(int64_t)s * a.ld + p] = (T)(1.0 / (ds * bn));
+                q[(int64_t)t * a.ld + p] = (T)(-1.0 / (dt * bn));
+            }
+        }
+        return;
+    }
+    if (s < 0 || (int64_t)s >= a.n || t < 0 || (int64_t)t >= a.n) {
+        atomicOr(a.err_flag, 1);
+        st.status[p] = RD_ERR_INVALID_ARG;
+        st.r[p] = NAN;
+        return;
+    }
+    if (s == t) {
+        st.status[p] = RD_OK;
+        st.r[p] = 0.0;
+        st.err[p] = 0.0;
+        return;
+    }
+    if (a.comp && a.comp[s] != a.comp[t]) {
+        st.status[p] = RD_ERR_DISCONNECTED;
+        st.r[p] = INFINITY;
+        return;
+    }
+    const double ds = a.deg64[s], dt = a.deg64[t];
+    const double b2 = 1.0 / ds + 1.0 / dt;
+    const double bn = sqrt(b2);
+    T* q = static_cast<T*>(a.qcur);
+    q[(int64_t)s * a.ld + p] = (T)(1.0 / (ds * bn));
+    q[(int64_t)t * a.ld + p] = (T)(-1.0 / (dt * bn));
+    st.b2[p] = b2;
+    st.err[p] = 1.0;
+    st.resid[p] = 1.0;
+    st.status[p] = RD_OK;
+    st.active[p] = 1;
+    atomicAdd(&st.act_count[0], 1);
+}
+
+void launch_init(cudaStream_t st, const InitArgs& a)
+{
+    const int nb = (a.npairs + 127) / 128;
+    if (a.elem_size == 8) k_init<double><<<nb, 128, 0, st>>>(a);
+    else k_init<float><<<nb, 128, 0, st>>>(a);
+}
+
+// -------------------------------------------------------------- finalise
+// Column p: reduce the SpMM block partials in block order, then
+//   alpha_i = <w, v_i>, beta_{i+1}^2 = ||w||^2 - alpha_i^2 - gamma^2 (gamma: component along
+//   D^{1/2}1, removed when deflating), and update the LDL^T factorisation of J_i = I - T_i:
+//   delta_1 = 1 - alpha_1,  delta_i = (1 - alpha_i) - beta_i^2 / delta_{i-1}
+//   g_1 = 1,                g_i = beta_i g_{i-1} / delta_{i-1}        (g = L^{-1} e_1)
+//   S_i = S_{i-1} + g_i^2 / delta_i = e_1^T J_i^{-1} e_1,   r_i = ||b||^2 S_i
+//   residual ||b - (I - Ahat) x_i|| / ||b|| = beta_{i+1} |g_i / delta_i|.
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
+{
+    __shared__ double part[3][8][32];
+    const int lane = threadIdx.x & 31, split = threadIdx.x >> 5;
+    const int64_t col = (int64_t)blockIdx.x * 32 + lane;
+    const PairState& st = a.st;
+    if (st.act_count[a.step] == 0) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (col < a.ld) {
+        const int64_t slab = col / a.tp, cin = col % a.tp;
+        for (int b = split; b < a.nblocks; b += 8) {
+            const double* bp = a.block_part + ((slab * a.nblocks + b) * 3) * a.tp + cin;
+            s0 += bp[0];
+            s1 += bp[a.tp];
+            s2 += bp[2 * a.tp];
+        }
+    }
+    part[0][split][lane] = s0;
+    part[1][split][lane] = s1;
+    part[2][split][lane] = s2;
+    __syncthreads();
+    if (split != 0 || col >= a.npairs) return;
+    const int p = (int)col;
+    if (!st.active[p]) return;
+    double A = 0.0, B = 0.0, C = 0.0;
+#pragma unroll
+    for (int sp = 0; sp < 8; ++sp) {
+        A += part[0][sp][lane];
+        B += part[1][sp][lane];
+        C += part[2][sp][lane];
+    }
+    const int j = a.step;       // 0-based step index; Lanczos step i = j + 1
+    const int64_t ld = a.ld;
+    T* cf = static_cast<T*>(a.cf_hist);
+    const double alpha = A;
+    const double beta_i = st.beta[p];
+    const double cdef = a.deflate ? C / a.sumdeg : 0.0;
+    const double gamma2 = a.deflate ? C * cdef : 0.0;
+    const double beta2 = B - alpha * alpha - gamma2;
+    double delta, g;
+    if (j == 0) {
+        delta = 1.0 - alpha;
+        g = 1.0;
+    } else {
+        const double dprev = st.delta[p];
+        delta = (1.0 - alpha) - beta_i * beta_i / dprev;
+        g = st.g[p] * beta_i / dprev;
+    }
+    const bool ok = isfinite(alpha) && isfinite(beta2) && isfinite(delta) && delta > 0.0;
+    if (!ok) {
+        st.status[p] = RD_ERR_NUMERIC;
+        st.active[p] = 0;
+        return;  // coefficients stay zero: the column is frozen at its last good estimate
+    }
+    const double incr = g * g / delta;
+    const double S = st.S[p] + incr;
+    st.S[p] = S;
+    st.r[p] = st.b2[p] * S;
+    st.ring[(int64_t)(j % kRing) * ld + p] = incr;
+    const double beta_next = sqrt(fmax(beta2, 0.0));
+    const double resid = beta_next * fabs(g / delta);
+    st.resid[p] = resid;
+    double tail = 0.0;
+    const int nr = j + 1 < kRing ? j + 1 : kRing;
+    for (int q = 0; q < nr; ++q) tail += st.ring[(int64_t)q * ld + p];
+    const double est = tail / S;
+    st.err[p] = est;
+    st.hist_alpha[(int64_t)j * ld + p] = alpha;
+    st.hist_beta[(int64_t)(j + 1) * ld + p] = beta_next;
+    st.k[p] = j + 1;
+    st.delta[p] = delta;
+    st.g[p] = g;
+
+    const double brk = a.fp64 ? 1e-12 : 1e-6;
+    bool stop = false;
+    if (beta_next <= brk * (fabs(alpha) + beta_i)) {
+        stop = true;  // Krylov space exhausted: T_i is exact
+        st.err[p] = 0.0;
+    } else if (!a.fixed_k) {
+        if (a.resid_tol > 0.0 && resid <= a.resid_tol) stop = true;
+        if (a.rel_tol > 0.0 && j + 1 >= kRing && est <= a.rel_tol) stop = true;
+    }
+    if (!stop && j + 1 >= a.k_max) {
+        stop = true;
+        if (!a.fixed_k) st.status[p] = RD_WARN_NOT_CONVERGED;
+    }
+    if (stop) {
+        st.active[p] = 0;
+        return;  // zero coefficients from here on (the history was zeroed at start)
+    }
+    cf[((int64_t)j * 4 + 1) * ld + p] = (T)alpha;
+    cf[((int64_t)j * 4 + 2) * ld + p] = (T)cdef;
+    cf[((int64_t)j * 4 + 3) * ld + p] = (T)(1.0 / beta_next);
+    cf[((int64_t)(j + 1) * 4 + 0) * ld + p] = (T)beta_next;
+    st.beta[p] = beta_next;
+    atomicAdd(&st.act_count[j + 1], 1);
+}
+
+void launch_finalize(cudaStream_t st, const FinArgs& a)
+{
+    const int nb = (int)((a.ld + 31) / 32);
+    if (a.elem_size == 8) k_finalize<double><<<nb, 256, 0, st>>>(a);
+    else k_finalize<float><<<nb, 256, 0, st>>>(a);
+}
+
+// ------------------------------------------------------------- normalise
+// q_{i+1} = (W - alpha_i q_i - c_i) / beta_{i+1}, written over W; optionally
+// phi += coef * q_i for the replay pass. 16-byte units; ld == 1 handled separately.
+template <typename T, bool LD1>
+__global__ void __launch_bounds__(256) k_normalize(const NormArgs<T> a)
+{
+    if (a.active_prev && *a.active_prev == 0) return;
+    constexpr int V = 16 / (int)sizeof(T);
+    const int64_t total = a.n * a.ld;
+    const int64_t units = total / V;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t ld = a.ld;
+    const T* cf_al = a.cf + ld;
+    const T* cf_c = a.cf + 2 * ld;
+    const T* cf_ib = a.cf + 3 * ld;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += stride) {
+        const int64_t e0 = u * V;
+        T w[V], qc[V], qn[V];
+        ld_stream<T, V>(w, a.w_to_qnext + e0);
+        ld_stream<T, V>(qc, a.qcur + e0);
+        if constexpr (LD1) {
+            const T al = cf_al[0], c = cf_c[0], ib = cf_ib[0];
+#pragma unroll
+            for (int i = 0; i < V; ++i) qn[i] = (w[i] - al * qc[i] - c) * ib;
+            if (a.phi) {
+                const T cf = a.coef[0];
+                T ph[V];
+                ld_plain<T, V>(ph, a.phi + e0);
+#pragma unroll
+                for (int i = 0; i < V; ++i) ph[i] += cf * qc[i];
+                st_plain<T, V>(a.phi + e0, ph);
+            }
+        } else {
+            const int64_t c0 = e0 % ld;
+            T al[V], c[V], ib[V];
+            ld_plain<T, V>(al, cf_al + c0);
+            ld_plain<T, V>(c, cf_c + c0);
+            ld_plain<T, V>(ib, cf_ib + c0);
+#pragma unroll
+            for (int i = 0; i < V; ++i) qn[i] = (w[i] - al[i] * qc[i] - c[i]) * ib[i];
+            if (a.phi) {
+                T cf[V], ph[V];
+                ld_plain<T, V>(cf, a.coef + c0);
+                ld_plain<T, V>(ph, a.phi + e0);
+#pragma unroll
+                for (int i = 0; i < V; ++i) ph[i] += cf[i] * qc[i];
+                st_plain<T, V>(a.phi + e0, ph);
+            }
+        }
+        st_plain<T, V>(a.w_to_qnext + e0, qn);
+    }
+    if constexpr (LD1) {
+        // scalar tail (ld == 1 and n not a multiple of V)
+        const int64_t t0 = units * V;
+        for (int64_t e = t0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+            const T w = a.w_to_qnext[e], qc = a.qcur[e];
+            a.w_to_qnext[e] = (w - a.cf[ld] * qc - a.cf[2 * ld]) * a.cf[3 * ld];
+            if (a.phi) a.phi[e] += a.coef[0] * qc;
+        }
+    }
+}
+
+template <typename T>
+static void launch_norm(int grid, cudaStream_t st, const NormArgs<T>& a)
+{
+    if (a.ld == 1) k_normalize<T, true><<<grid, 256, 0, st>>>(a);
+    else k_normalize<T, false><<<grid, 256, 0, st>>>(a);
+}
+
+void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a) { launch_norm<float>(grid, st, a); }
+void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a) { launch_norm<double>(grid, st, a); }
+
+// ---------------------------------------------------------------- output
+__global__ void k_output(const OutArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs) return;
+    const PairState& st = a.st;
+    const int status = st.status[p];
+    a.r_out[p] = st.r[p];
+    if (a.iters_out) a.iters_out[p] = st.k[p];
+    if (a.err_out) a.err_out[p] = st.err[p];
+    if (a.status_out) a.status_out[p] = status;
+    if (status == RD_WARN_NOT_CONVERGED) atomicOr(&a.summary[0], 1);
+    if (status == RD_ERR_NUMERIC) atomicOr(&a.summary[1], 1);
+}
+
+void launch_output(cudaStream_t st, const OutArgs& a)
+{
+    k_output<<<(a.npairs + 127) / 128, 128, 0, st>>>(a);
+}
+
+// ---------------------------------------------------- tridiagonal solve
+// z = (I - T_k)^{-1} e_1 per pair from the stored alpha_1..alpha_k, beta_2..beta_k by
+// forward elimination and back substitution (I - T_k is SPD, so no pivoting);
+// coef_j = ||b|| z_j is the weight of q_j in the potential
+// phi = ||b|| D^{-1/2} V_k z (Algorithm 5, first line). Also writes gbar[p], the upstream
+// gradient of pair p (0 for pairs without a finite result and for padding columns).
+template <typename T>
+__global__ void k_zsolve(const ZsolveArgs a)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.ld) return;
+    T* coef = static_cast<T*>(a.coef_hist);
+    T* gbar = static_cast<T*>(a.gbar);
+    const PairState& st = a.st;
+    const int64_t ld = a.ld;
+    const int status = p < a.npairs ? st.status[p] : RD_ERR_INVALID_ARG;
+    const int k = p < a.npairs ? st.k[p] : 0;
+    const bool use = (status == RD_OK || status == RD_WARN_NOT_CONVERGED) && k > 0;
+    if (!use) {
+        for (int j = 0; j < a.k_max; ++j) coef[(int64_t)j * ld + p] = T(0);
+        gbar[p] = T(0);
+        return;
+    }
+    gbar[p] = (T)(a.grad_r ? a.grad_r[p] : 1.0);
+    double* zs = a.zscratch;  // [k_max][2][ld]: c'_j, d'_j
+    const double* al = st.hist_alpha;
+    const double* be = st.hist_beta;  // be[j*ld + p] = beta_{j+1}
+    double cprev = 0.0, dprev = 0.0;
+    for (int j = 0; j < k; ++j) {
+        const double lower = j > 0 ? -be[(int64_t)j * ld + p] : 0.0;
+        const double m = (1.0 - al[(int64_t)j * ld + p]) - lower * cprev;
+        const double c = (j + 1 < k) ? -be[(int64_t)(j + 1) * ld + p] / m : 0.0;
+        const double d = ((j == 0 ? 1.0 : 0.0) - lower * dprev) / m;
+        zs[((int64_t)j * 2) * ld + p] = c;
+        zs[((int64_t)j * 2 + 1) * ld + p] = d;
+        cprev = c;
+        dprev = d;
+    }
+    const double bn = sqrt(st.b2[p]);
+    double x = 0.0;
+    for (int j = k - 1; j >= 0; --j) {
+        x = zs[((int64_t)j * 2 + 1) * ld + p] - zs[((int64_t)j * 2) * ld + p] * x;
+        coef[(int64_t)j * ld + p] = (T)(bn * x);
+    }
+    for (int j = k; j < a.k_max; ++j) coef[(int64_t)j * ld + p] = T(0);
+}
+
+void launch_zsolve(cudaStream_t st, const ZsolveArgs& a)
+{
+    const int nb = (int)((a.ld + 127) / 128);
+    if (a.elem_size == 8) k_zsolve<double><<<nb, 128, 0, st>>>(a);
+    else k_zsolve<float><<<nb, 128, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------- edge gradient
+// grad[e] = -1/2 sum_p gbar_p (phi_p(u) - phi_p(v))^2 for stored entry e = (u -> v).
+// A row group of GS lanes spans VEC*GS columns and loops over the column chunks.
+template <typename T, int VEC, int GS>
+__global__ void __launch_bounds__(256) k_edge_grad(const EdgeGradArgs<T> a)
+{
+    constexpr int TP = VEC * GS;
+    constexpr int RPW = 32 / GS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cl = lane % GS, rs = lane / GS;
+    const unsigned mask = group_mask<GS, 1>(lane);
+    const int64_t nslots = (int64_t)gridDim.x * (blockDim.x / 32) * RPW;
+    const int64_t slot0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + warp) * RPW + rs;
+    const int nch = (int)(a.ld / TP);
+    for (int64_t row = slot0; row < a.n; row += nslots) {
+        const int64_t beg = a.row_ptr[row], end = a.row_ptr[row + 1];
+        for (int64_t e = beg; e < end; ++e) {
+            const int64_t v = __ldg(a.col + e);
+            float s = 0.f;
+            for (int ch = 0; ch < nch; ++ch) {
+                const int64_t c0 = (int64_t)ch * TP + cl * VEC;
+                T pu[VEC], pv[VEC], gb[VEC];
+                ld_gather<T, VEC>(pu, a.phi + row * a.ld + c0);
+                ld_gather<T, VEC>(pv, a.phi + v * a.ld + c0);
+                ld_gather<T, VEC>(gb, a.gbar + c0);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    const T d = pu[i] - pv[i];
+                    s += (float)(gb[i] * d * d);
+                }
+            }
+#pragma unroll
+            for (int off = 1; off < GS; off <<= 1) s += __shfl_xor_sync(mask, s, off);
+            if (cl == 0) a.grad_out[e] = -0.5f * s;
+        }
+    }
+}
+
+template <typename T>
+static void launch_eg(int grid, cudaStream_t st, const EdgeGradArgs<T>& a)
+{
+    constexpr int VEC = 16 / (int)sizeof(T);
+    const int64_t units = a.ld / VEC;  // ld is a multiple of VEC here
+    if (units % 32 == 0) k_edge_grad<T, VEC, 32><<<grid, 256, 0, st>>>(a);
+    else if (units % 16 == 0) k_edge_grad<T, VEC, 16><<<grid, 256, 0, st>>>(a);
+    else if (units % 8 == 0) k_edge_grad<T, VEC, 8><<<grid, 256, 0, st>>>(a);
+    else if (units % 4 == 0) k_edge_grad<T, VEC, 4><<<grid, 256, 0, st>>>(a);
+    else if (units % 2 == 0) k_edge_grad<T, VEC, 2><<<grid, 256, 0, st>>>(a);
+    else k_edge_grad<T, VEC, 1><<<grid, 256, 0, st>>>(a);
+}
+
+void launch_edge_grad_f32(int grid, cudaStream_t st, const EdgeGradArgs<float>& a) { launch_eg<float>(grid, st, a); }
+void launch_edge_grad_f64(int grid, cudaStream_t st, const EdgeGradArgs<double>& a) { launch_eg<double>(grid, st, a); }
+
+}  // namespace rd

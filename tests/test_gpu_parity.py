@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path (called through the C ABI via the thin binding) against
+the CPU oracle on the same seeded inputs.
+
+Tolerances: FP64 mode within 1e-9 relative of the oracle, FP32-vector mode within
+1e-5 relative (the bars fixed for this method's two precision modes).
+"""
+import numpy as np
+import pytest
+
+from graphgen import families as F
+from graphgen import workloads as W
+from graphgen.graph import to_csr
+from oracle import dense, lanczos
+from tests import closed_forms as CF
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rd():
+    import torch
+
+    assert torch.cuda.is_available()
+    import paper_2601_11159_gb300 as rd
+
+    rd.lib()  # fails loudly if the library is not built
+    return rd
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b) / np.abs(b)
+
+
+SMALL = [
+    ("K7", lambda: F.complete(7)),
+    ("C11", lambda: F.cycle(11)),
+    ("P9", lambda: F.path(9)),
+    ("toy", lambda: F.toy_graph()),
+    ("grid8", lambda: F.grid(8)),
+    ("grid5x7", lambda: F.grid(5, 7)),
+    ("rc60u", lambda: F.random_connected(60, 100, 3, None)),
+    ("rc70w", lambda: F.random_connected(70, 140, 5, "uniform")),
+    ("rc80ln", lambda: F.random_connected(80, 200, 7, "lognormal")),
+]
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_small_graphs_vs_dense(rd, name, make, mode):
+    g = make()
+    s, t = F.random_pairs(g.n, 9, 17)
+    ref = dense.DenseRD.of(g).r(s, t)
+    G = rd.Graph.from_csr(g)
+    tol = FP64_TOL if mode == "fp64" else FP32_TOL
+    res = G.query(s, t, mode=mode, k_max=400, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6)
+    assert np.all(res.status >= 0), res.status
+    assert rel(res.r, ref).max() < tol, (name, mode, rel(res.r, ref).max())
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_fixed_k_matches_oracle_history(rd, mode, tol):
+    """Same k, same recurrence: the GPU estimate after k steps equals the oracle's rhat_k."""
+    g = F.grid_deleted(24, 0.05, 9)
+    s, t = F.random_pairs(g.n, 5, 2)
+    G = rd.Graph.from_csr(g)
+    for k in [1, 2, 5, 12, 30]:
+        res = G.query(s, t, mode=mode, k_max=k, fixed_k=True)
+        assert np.all(res.iters == k)
+        ref = np.array([lanczos.lanczos_pair(g, int(a), int(b), k_max=k)["r"] for a, b in zip(s, t)])
+        assert rel(res.r, ref).max() < tol, (k, rel(res.r, ref).max())
+
+
+def test_grid64_corner_fp64_closed_form(rd):
+    """64x64 grid, s = 0, t = 4095, FP64, k <= 500 or relative residual 1e-10."""
+    g, s, t = W.grid64()
+    ref = CF.grid_r(64, 64, 0, 4095)
+    G = rd.Graph.from_csr(g)
+    res = G.query(s, t, mode="fp64", k_max=500, rel_tol=0.0, resid_tol=1e-10)
+    assert res.status[0] == 0 and res.iters[0] < 500
+    assert rel(res.r, [ref]).max() < FP64_TOL
+    # the same with the single-vector SpMV path
+    res1 = G.query(s, t, mode="fp64", k_max=500, rel_tol=0.0, resid_tol=1e-10, plain=True)
+    assert rel(res1.r, [ref]).max() < FP64_TOL
+
+
+def test_ragged_batch_edge_cases(rd):
+    g = F.random_connected(300, 500, 4, "uniform")
+    n = g.n
+    s, t = F.random_pairs(n, 37, 8)          # 37 pairs: not a multiple of any tile
+    s[3] = t[3]                              # s == t
+    s[10], t[10] = 0, n - 1                  # extreme ids
+    ref = dense.DenseRD.of(g).r(s, t)
+    G = rd.Graph.from_csr(g)
+    for mode, tol in [("fp64", FP64_TOL), ("fp32", FP32_TOL)]:
+        res = G.query(s, t, mode=mode, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6)
+        assert res.r[3] == 0.0 and res.iters[3] == 0 and res.status[3] == 0
+        m = np.arange(37) != 3
+        assert rel(res.r[m], ref[m]).max() < tol
+    empty = G.query(np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert empty.r.size == 0
+
+
+def test_disconnected_and_invalid(rd):
+    a = F.cycle(6)
+    b = F.path(5)
+    ea, eb, _ = a.undirected_edges()
+    fa, fb, _ = b.undirected_edges()
+    g = to_csr(11, np.concatenate([ea, fa + 6]), np.concatenate([eb, fb + 6]))
+    G = rd.Graph.from_csr(g)
+    assert G.ncomponents == 2
+    res = G.query(np.array([0, 6, 1], np.int32), np.array([3, 10, 8], np.int32), mode="fp64", rel_tol=1e-12)
+    assert res.r[0] == pytest.approx(CF.cycle_r(6, 3), rel=1e-9)
+    assert res.r[1] == pytest.approx(4.0, rel=1e-9)
+    assert np.isinf(res.r[2]) and res.status[2] == rd.RD_ERR_DISCONNECTED
+    with pytest.raises(rd.RDError):
+        G.query(np.array([0], np.int32), np.array([11], np.int32))
+    with pytest.raises(rd.RDError):
+        G.query(np.array([-1], np.int32), np.array([2], np.int32))
+
+
+def test_bad_graphs_rejected(rd):
+    g = F.path(4)
+    with pytest.raises(rd.RDError):
+        rd.Graph(g.row_ptr, np.array([1, 0, 2, 1, 3, 9], np.int32))           # column out of range
+    with pytest.raises(rd.RDError):
+        rd.Graph(g.row_ptr, g.col, np.array([1, 1, -1, 1, 1, 1], np.float32))  # negative weight
+    with pytest.raises(rd.RDError):
+        rd.Graph(np.array([0, 1, 2, 2], np.int64), np.array([1, 0], np.int32))  # isolated vertex 2
+    asym = to_csr(3, np.array([0, 1]), np.array([1, 2]), np.array([1.0, 2.0], np.float32))
+    w = asym.w.copy()
+    w[0] = 5.0
+    with pytest.raises(rd.RDError):
+        rd.Graph(asym.row_ptr, asym.col, w, check_symmetry=True)
+
+
+def test_self_loops_dropped(rd):
+    g = F.random_connected(40, 60, 2, "uniform")
+    rows = g.rows()
+    # insert a self-loop at every vertex
+    ra = np.concatenate([rows, np.arange(g.n)])
+    ca = np.concatenate([g.col.astype(np.int64), np.arange(g.n)])
+    wa = np.concatenate([g.w, np.full(g.n, 3.0, np.float32)])
+    order = np.lexsort((ca, ra))
+    rp = np.zeros(g.n + 1, np.int64)
+    np.cumsum(np.bincount(ra, minlength=g.n), out=rp[1:])
+    G = rd.Graph(rp, ca[order].astype(np.int32), wa[order])
+    assert G.nnz == g.nnz
+    s, t = F.random_pairs(g.n, 5, 1)
+    res = G.query(s, t, mode="fp64", rel_tol=0.0, resid_tol=1e-12)
+    assert rel(res.r, dense.DenseRD.of(g).r(s, t)).max() < FP64_TOL
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_batched_vs_plain_and_order(rd, mode, tol):
+    g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 40, 77)
+    G = rd.Graph.from_csr(g)
+    kw = dict(mode=mode, k_max=60, fixed_k=True)
+    b = G.query(s, t, **kw)
+    p = G.query(s, t, plain=True, **kw)
+    assert rel(b.r, p.r).max() < tol
+    perm = np.random.default_rng(0).permutation(len(s))
+    bp = G.query(s[perm], t[perm], **kw)
+    assert np.array_equal(bp.r, b.r[perm])      # same batch size: bitwise equal per pair
+    again = G.query(s, t, **kw)
+    assert np.array_equal(again.r, b.r)          # deterministic
+
+
+def test_scaling_by_four_is_bitwise(rd):
+    g = F.grid_deleted(30, 0.05, 5)
+    s, t = F.random_pairs(g.n, 8, 3)
+    G1 = rd.Graph.from_csr(g)
+    G4 = rd.Graph(g.row_ptr, g.col, (4.0 * g.w).astype(np.float32))
+    for mode in ["fp64", "fp32"]:
+        r1 = G1.query(s, t, mode=mode, k_max=40, fixed_k=True).r
+        r4 = G4.query(s, t, mode=mode, k_max=40, fixed_k=True).r
+        assert np.array_equal(r4 * 4.0, r1)
+
+
+def test_symmetry_in_s_t(rd):
+    g = F.random_connected(200, 400, 12, "lognormal")
+    s, t = F.random_pairs(g.n, 16, 5)
+    G = rd.Graph.from_csr(g)
+    a = G.query(s, t, mode="fp64", rel_tol=0.0, resid_tol=1e-12).r
+    b = G.query(t, s, mode="fp64", rel_tol=0.0, resid_tol=1e-12).r
+    assert rel(a, b).max() < 1e-10
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-8), ("fp32", 2e-4)])
+def test_edge_grad_vs_dense(rd, mode, tol):
+    g = F.random_connected(120, 260, 31, "lognormal")
+    s, t = F.random_pairs(g.n, 6, 9)
+    gbar = np.linspace(-1.0, 2.0, 6)
+    D = dense.DenseRD.of(g)
+    ref = D.edge_grad(s, t, gbar)
+    G = rd.Graph.from_csr(g)
+    gw, r = G.edge_grad(s, t, gbar, mode=mode, k_max=400, rel_tol=0.0,
+                        resid_tol=1e-13 if mode == "fp64" else 1e-6)
+    assert rel(r, D.r(s, t)).max() < (FP64_TOL if mode == "fp64" else FP32_TOL)
+    scale = np.abs(ref).max()
+    assert np.abs(gw - ref).max() / scale < tol, np.abs(gw - ref).max() / scale
+
+
+def test_potential_vs_dense(rd):
+    g = F.random_connected(90, 200, 13, "uniform")
+    s, t = F.random_pairs(g.n, 4, 6)
+    D = dense.DenseRD.of(g)
+    G = rd.Graph.from_csr(g)
+    phi, r = G.potential(s, t, mode="fp64", rel_tol=0.0, resid_tol=1e-13)
+    for p in range(4):
+        ref = D.potential(int(s[p]), int(t[p]))
+        got = phi[p].astype(np.float64)
+        # defined up to a constant: compare edge differences
+        rows = g.rows()
+        d_ref = ref[rows] - ref[g.col]
+        d_got = got[rows] - got[g.col]
+        assert np.abs(d_got - d_ref).max() < 1e-6 * np.abs(d_ref).max()
+
+
+def test_torch_device_io_and_autograd(rd):
+    import torch
+
+    g = F.random_connected(100, 220, 19, "uniform")
+    s, t = F.random_pairs(g.n, 5, 4)
+    G = rd.Graph.from_csr(g)
+    sd = torch.from_numpy(s).cuda()
+    td = torch.from_numpy(t).cuda()
+    res = G.query(sd, td, mode="fp64", rel_tol=0.0, resid_tol=1e-12)
+    assert res.r.is_cuda
+    ref = dense.DenseRD.of(g).r(s, t)
+    assert rel(res.r.cpu().numpy(), ref).max() < FP64_TOL
+    w = torch.from_numpy(g.w).cuda().requires_grad_(True)
+    opts = dict(mode="fp64", rel_tol=0.0, resid_tol=1e-13)
+    r = rd.ResistanceDistance.apply(w, G, sd, td, opts)
+    loss = (r * torch.arange(1, 6, device="cuda", dtype=torch.float64)).sum()
+    loss.backward()
+    refg = dense.DenseRD.of(g).edge_grad(s, t, np.arange(1, 6, dtype=np.float64))
+    got = w.grad.cpu().numpy().astype(np.float64)
+    assert np.abs(got - refg).max() / np.abs(refg).max() < 1e-6
