@@ -87,6 +87,8 @@ typedef struct {
     int32_t rows_per_warp; /* rows a warp works on at once; 0 = tuned */
     int32_t chunk_steps;   /* steps between host convergence polls; 0 = default (8) */
     uint32_t flags;        /* RD_Q_* */
+    int32_t kernel;        /* SpMM kernel: 0 = tuned, 1 = row-group (warp lanes split a row's
+                              nonzeros), 2 = row-stream (row groups walk runs of consecutive rows) */
 } rd_query_opts;
 
 /* Per-call statistics of the last rd_query / rd_edge_grad / rd_potential on g. */
@@ -98,13 +100,14 @@ typedef struct {
     int32_t rhs_tile;        /* configuration used */
     int32_t rows_per_warp;
     int32_t nnz_lanes;       /* lanes that share one row's nonzeros */
+    int32_t kernel;          /* SpMM kernel used (1 = row-group, 2 = row-stream) */
     int64_t ld;              /* padded number of right-hand-side columns (vector row stride) */
     double spmm_bytes;       /* algorithmic bytes of one SpMM launch: 4*nnz (+4*nnz weights)
                                 + 8*(n+1) + 3*ld*n*sizeof(element) */
 } rd_call_stats;
 
 /* Fill `opts` with defaults: k_max 1000, rel_tol 1e-7, resid_tol 0, FP32 vectors with FP64
- * scalars, tuned tiles, chunk 8, flags 0. */
+ * scalars, tuned tiles and kernel, chunk 8, flags 0. */
 void rd_query_opts_init(rd_query_opts* opts);
 
 /* Build a device graph from symmetric CSR (Section 2.1: undirected graph; weighted

@@ -100,7 +100,7 @@ def _check(st: int, where: str, ok=(RD_OK, RD_WARN_NOT_CONVERGED)):
 
 
 def _opts(k_max=1000, rel_tol=1e-7, resid_tol=0.0, mode="fp32", rhs_tile=0, rows_per_warp=0, chunk_steps=0,
-          fixed_k=False, deflate=True, plain=False, profile=False) -> _lib.QueryOpts:
+          fixed_k=False, deflate=True, plain=False, profile=False, kernel=0) -> _lib.QueryOpts:
     o = _lib.QueryOpts()
     lib().rd_query_opts_init(C.byref(o))
     o.k_max = int(k_max)
@@ -115,6 +115,7 @@ def _opts(k_max=1000, rel_tol=1e-7, resid_tol=0.0, mode="fp32", rhs_tile=0, rows
     o.rhs_tile = int(rhs_tile)
     o.rows_per_warp = int(rows_per_warp)
     o.chunk_steps = int(chunk_steps)
+    o.kernel = {"tuned": 0, "group": 1, "stream": 2}.get(kernel, kernel) if isinstance(kernel, str) else int(kernel)
     o.flags = ((RD_Q_FIXED_K if fixed_k else 0) | (0 if deflate else RD_Q_NO_DEFLATE) |
                (RD_Q_PLAIN if plain else 0) | (RD_Q_PROFILE if profile else 0))
     return o

@@ -45,6 +45,7 @@ class QueryOpts(C.Structure):
         ("rows_per_warp", C.c_int32),
         ("chunk_steps", C.c_int32),
         ("flags", C.c_uint32),
+        ("kernel", C.c_int32),
     ]
 
 
@@ -57,6 +58,7 @@ class CallStats(C.Structure):
         ("rhs_tile", C.c_int32),
         ("rows_per_warp", C.c_int32),
         ("nnz_lanes", C.c_int32),
+        ("kernel", C.c_int32),
         ("ld", C.c_int64),
         ("spmm_bytes", C.c_double),
     ]

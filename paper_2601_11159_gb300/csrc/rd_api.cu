@@ -103,7 +103,7 @@ static void free_graph(rd_graph* g)
 {
     if (!g) return;
     void* ptrs[] = {g->row_ptr, g->col, g->w, g->keep_idx, g->deg64, g->invdeg64, g->deg32, g->invdeg32,
-                    g->comp, g->heavy_rows, g->heavy_first, g->chunk_beg, g->chunk_end, g->ws.base};
+                    g->comp, g->heavy_rows, g->heavy_first, g->chunk_beg, g->chunk_end, g->task_row, g->ws.base};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
@@ -159,6 +159,29 @@ static rd_status build_heavy(rd_graph* g, const std::vector<int64_t>& rp)
     }
     g->n_heavy_rows = (int64_t)rows.size();
     g->n_chunks = (int64_t)cb.size();
+    // row-stream tasks: greedy runs of consecutive light rows with at most task_nnz nonzeros
+    // (a single light row longer than that stays whole); each heavy row is a task of its own
+    std::vector<int32_t> tasks;
+    tasks.push_back(0);
+    int64_t cur = 0;
+    for (int64_t u = 0; u < g->n; ++u) {
+        const int64_t d = rp[u + 1] - rp[u];
+        if (d > g->heavy_thr) {
+            if (tasks.back() != (int32_t)u) tasks.push_back((int32_t)u);
+            tasks.push_back((int32_t)(u + 1));
+            cur = 0;
+            continue;
+        }
+        if (cur > 0 && cur + d > g->task_nnz) {
+            tasks.push_back((int32_t)u);
+            cur = 0;
+        }
+        cur += d;
+    }
+    if (tasks.back() != (int32_t)g->n) tasks.push_back((int32_t)g->n);
+    g->ntasks = (int64_t)tasks.size() - 1;
+    RD_CUDA(cudaMalloc((void**)&g->task_row, sizeof(int32_t) * tasks.size()));
+    RD_CUDA(cudaMemcpy(g->task_row, tasks.data(), sizeof(int32_t) * tasks.size(), cudaMemcpyHostToDevice));
     if (g->n_heavy_rows == 0) return RD_OK;
     RD_CUDA(cudaMalloc((void**)&g->heavy_rows, sizeof(int32_t) * rows.size()));
     RD_CUDA(cudaMalloc((void**)&g->heavy_first, sizeof(int32_t) * first.size()));
@@ -289,6 +312,11 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     if (plain || P == 1) {
         c.vec = 1;
         c.gs = 1;
+        if (o.kernel == 2) {  // row-stream with one lane per task
+            c.nzl = 1;
+            c.kind = 1;
+            return c;
+        }
         c.nzl = mdeg <= 6 ? 4 : (mdeg <= 12 ? 8 : (mdeg <= 24 ? 16 : 32));
         if (o.rows_per_warp > 0) c.nzl = std::max(1, std::min(32, 32 / o.rows_per_warp));
         return c;
@@ -301,7 +329,8 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     c.vec = fp64 ? (tp >= 128 ? 4 : 2) : (tp >= 256 ? 8 : 4);
     c.gs = std::max(1, tp / c.vec);
     c.nzl = 1;
-    if (o.rows_per_warp > 0) c.nzl = std::max(1, 32 / (c.gs * o.rows_per_warp));
+    c.kind = o.kernel == 1 ? 0 : 1;  // row-stream unless the row-group kernel is asked for
+    if (c.kind == 0 && o.rows_per_warp > 0) c.nzl = std::max(1, 32 / (c.gs * o.rows_per_warp));
     return c;
 }
 
@@ -323,15 +352,16 @@ static rd_status make_plan(rd_graph* g, int64_t P, const rd_query_opts& o, bool 
     int bps = spmm_blocks_per_sm(pl->cfg, g->weighted, false, pl->fp64);
     if (bps < 1) bps = 1;
     int64_t gm = (int64_t)bps * g->sm_count;
-    gm = std::min<int64_t>(gm, (g->n + rows_per_block - 1) / rows_per_block);
+    const int64_t units = pl->cfg.kind == 1 ? g->ntasks : g->n;  // rows or tasks, one per row group
+    gm = std::min<int64_t>(gm, (units + rows_per_block - 1) / rows_per_block);
     pl->grid_main = (int)std::max<int64_t>(gm, 1);
     int bph = spmm_blocks_per_sm(pl->cfg, g->weighted, true, pl->fp64);
     if (bph < 1) bph = 1;
     int64_t gh = (int64_t)bph * g->sm_count;
     gh = std::min<int64_t>(gh, (g->n_chunks + rows_per_block - 1) / rows_per_block);
     pl->grid_heavy = (int)std::max<int64_t>(gh, 1);
-    const int64_t units = (g->n * pl->ld) / (16 / (int64_t)pl->elem) + 1;
-    pl->grid_norm = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 8, (units + 255) / 256));
+    const int64_t vunits = (g->n * pl->ld) / (16 / (int64_t)pl->elem) + 1;
+    pl->grid_norm = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 8, (vunits + 255) / 256));
     return RD_OK;
 }
 
@@ -470,6 +500,8 @@ static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
     a.chunk_beg = g->chunk_beg;
     a.chunk_end = g->chunk_end;
     a.heavy_part = static_cast<T*>(c.b.heavy_part);
+    a.ntasks = g->ntasks;
+    a.task_row = g->task_row;
     a.block_part = c.b.block_part;
     a.active_prev = reduce ? c.b.st.act_count + j : nullptr;
     a.do_reduce = reduce ? 1 : 0;
@@ -644,6 +676,7 @@ static void record_stats(RunCtx& c)
     s.rhs_tile = c.pl.cfg.tp();
     s.rows_per_warp = c.pl.cfg.rpw();
     s.nnz_lanes = c.pl.cfg.nzl;
+    s.kernel = c.pl.cfg.kind == 1 ? 2 : 1;
     s.ld = c.pl.ld;
     const double nnz = (double)c.g->nnz;
     s.spmm_bytes = 4.0 * nnz + (c.g->weighted ? 4.0 * nnz : 0.0) + 8.0 * (double)(c.g->n + 1) +
@@ -678,6 +711,10 @@ static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t
     else rd_query_opts_init(o);
     if (o->k_max < 1 || o->k_max > (1 << 22)) {
         set_error("k_max must be in [1, 2^22]");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (o->kernel < 0 || o->kernel > 2) {
+        set_error("kernel must be 0, 1 or 2");
         return RD_ERR_INVALID_ARG;
     }
     if (o->mode != RD_MODE_FP64 && o->mode != RD_MODE_FP32V_FP64S) {
@@ -804,6 +841,7 @@ void rd_query_opts_init(rd_query_opts* o)
     o->rows_per_warp = 0;
     o->chunk_steps = 8;
     o->flags = 0;
+    o->kernel = 0;
 }
 
 const char* rd_status_string(rd_status s)

@@ -33,11 +33,16 @@ rd_status cuda_status(cudaError_t e, const char* what);
 // right-hand-side tile (VEC elements each, so the tile is TP = VEC*GS
 // columns); NZL lanes share the nonzeros of one row; RPW = 32/(GS*NZL) rows
 // are in flight per warp.
+// kind 0: row-group kernel (k_spmm, grid-stride over rows); kind 1: row-stream kernel
+// (k_spmm_rows, grid-stride over tasks of consecutive rows; nzl must be 1).
 struct SpmmCfg {
-    int vec = 4, gs = 32, nzl = 1;
+    int vec = 4, gs = 32, nzl = 1, kind = 0;
     int tp() const { return vec * gs; }
     int rpw() const { return 32 / (gs * nzl); }
-    bool operator==(const SpmmCfg& o) const { return vec == o.vec && gs == o.gs && nzl == o.nzl; }
+    bool operator==(const SpmmCfg& o) const
+    {
+        return vec == o.vec && gs == o.gs && nzl == o.nzl && kind == o.kind;
+    }
 };
 
 constexpr int kBlock = 256;        // threads per block of the SpMM kernels
@@ -64,6 +69,8 @@ struct StepArgs {
     const int32_t* chunk_beg;      // nnz range of each chunk
     const int32_t* chunk_end;
     T* heavy_part;                 // n_chunks x ld
+    int64_t ntasks;                // row-stream tasks: rows [task_row[i], task_row[i+1])
+    const int32_t* task_row;
     double* block_part;            // [slab][block][3][TP]
     const int32_t* active_prev;    // early exit when *active_prev == 0 (nullable)
     int do_reduce;
@@ -140,6 +147,10 @@ struct rd_graph {
     int32_t* heavy_first = nullptr;
     int32_t* chunk_beg = nullptr;
     int32_t* chunk_end = nullptr;
+    // row-stream tasks: consecutive rows with at most task_nnz nonzeros, heavy rows alone
+    int task_nnz = 512;
+    int64_t ntasks = 0;
+    int32_t* task_row = nullptr;
     double mean_deg = 0.0;
     rd::Workspace ws;
     rd_call_stats stats{};

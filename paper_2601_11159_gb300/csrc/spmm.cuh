@@ -158,47 +158,49 @@ struct Acc<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
-// Sum over the nonzeros [e0, end) with stride NZL of w_e * q[col_e, c0 .. c0+VEC).
-template <typename T, int VEC, int NZL, bool WEIGHTED>
-__device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t e, int64_t end, int64_t c0,
-                                           T (&acc)[VEC])
+// Independent gathers in flight per lane per round: 8 for 16-byte lanes, 4 for wider ones.
+template <typename T, int VEC>
+inline constexpr int kUnroll = (int)sizeof(T) * VEC > 16 ? 4 : 8;
+
+// Sum over the nonzeros [beg, end) of w_e * q[col_e, c0 .. c0+VEC), shared by the G = GS*NZL
+// lanes of a row group: the group loads up to G column indices (and weights) with one
+// coalesced load, broadcasts them by shuffle, and each of the NZL nonzero lanes issues U
+// independent gathers per round (nonzero k of the chunk goes to lane zl = k % NZL).
+template <typename T, int VEC, int GS, int NZL, int U, bool WEIGHTED>
+__device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t beg, int64_t end, int64_t c0, int li,
+                                           int zl, unsigned mask, T (&acc)[VEC])
 {
+    constexpr int G = GS * NZL;
     const T* __restrict__ q = a.qcur + c0;
     const int64_t ld = a.ld;
-    for (; e + 3 * NZL < end; e += 4 * NZL) {
-        const int64_t j0 = __ldg(a.col + e), j1 = __ldg(a.col + e + NZL);
-        const int64_t j2 = __ldg(a.col + e + 2 * NZL), j3 = __ldg(a.col + e + 3 * NZL);
-        T x0[VEC], x1[VEC], x2[VEC], x3[VEC];
-        ld_gather<T, VEC>(x0, q + j0 * ld);
-        ld_gather<T, VEC>(x1, q + j1 * ld);
-        ld_gather<T, VEC>(x2, q + j2 * ld);
-        ld_gather<T, VEC>(x3, q + j3 * ld);
-        if constexpr (WEIGHTED) {
-            const T w0 = (T)__ldg(a.w + e), w1 = (T)__ldg(a.w + e + NZL);
-            const T w2 = (T)__ldg(a.w + e + 2 * NZL), w3 = (T)__ldg(a.w + e + 3 * NZL);
+    for (int64_t base = beg; base < end; base += G) {
+        const int cnt = (int)(end - base < G ? end - base : G);
+        const int my_col = li < cnt ? __ldg(a.col + base + li) : 0;
+        float my_w = 1.0f;
+        if constexpr (WEIGHTED) my_w = li < cnt ? __ldg(a.w + base + li) : 0.0f;
+        for (int k0 = 0; k0 < cnt; k0 += NZL * U) {
+            T x[U][VEC];
+            T wu[U];
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) {
-                acc[i] += w0 * x0[i];
-                acc[i] += w1 * x1[i];
-                acc[i] += w2 * x2[i];
-                acc[i] += w3 * x3[i];
+            for (int u = 0; u < U; ++u) {
+                const int kk = k0 + zl + u * NZL;
+                const int j = __shfl_sync(mask, my_col, kk & (G - 1), G);
+                if constexpr (WEIGHTED) wu[u] = (T)__shfl_sync(mask, my_w, kk & (G - 1), G);
+                if (kk < cnt) {
+                    ld_gather<T, VEC>(x[u], q + (int64_t)j * ld);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) x[u][i] = T(0);
+                }
             }
-        } else {
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) acc[i] += (x0[i] + x1[i]) + (x2[i] + x3[i]);
-        }
-    }
-    for (; e < end; e += NZL) {
-        const int64_t j0 = __ldg(a.col + e);
-        T x0[VEC];
-        ld_gather<T, VEC>(x0, q + j0 * ld);
-        if constexpr (WEIGHTED) {
-            const T w0 = (T)__ldg(a.w + e);
+            for (int u = 0; u < U; ++u) {
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) acc[i] += w0 * x0[i];
-        } else {
-#pragma unroll
-            for (int i = 0; i < VEC; ++i) acc[i] += x0[i];
+                for (int i = 0; i < VEC; ++i) {
+                    if constexpr (WEIGHTED) acc[i] += wu[u] * x[u][i];
+                    else acc[i] += x[u][i];
+                }
+            }
         }
     }
 }
@@ -225,6 +227,79 @@ __device__ __forceinline__ unsigned group_mask(int lane)
     }
 }
 
+// Block partial sums of the three reductions for one slab: lanes holding the same
+// columns are combined by an xor-shuffle tree (fixed order), then warps in warp order.
+template <typename T, int VEC, int GW, int TP>
+__device__ __forceinline__ void block_partials(const StepArgs<T>& a, const Acc<T> (&sA)[VEC], const Acc<T> (&sB)[VEC],
+                                               const Acc<T> (&sC)[VEC], double (&red)[kWarps][TP], int slab,
+                                               int lane, int warp, int cl)
+{
+#pragma unroll
+    for (int qn = 0; qn < 3; ++qn) {
+        double v[VEC];
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) v[i] = qn == 0 ? sA[i].value() : (qn == 1 ? sB[i].value() : sC[i].value());
+#pragma unroll
+        for (int off = GW; off < 32; off <<= 1) {
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+        }
+        if (lane < TP / VEC) {
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) red[warp][cl * VEC + i] = v[i];
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < TP; c += kBlock) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) sum += red[w][c];
+            a.block_part[(((int64_t)slab * gridDim.x + blockIdx.x) * 3 + qn) * TP + c] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// Epilogue of one row: W = invd * acc - beta * q_prev written over q_prev, and the
+// row's terms of sum d W q_cur, sum d W^2, sum d W added to the lane's accumulators.
+template <typename T, int VEC>
+__device__ __forceinline__ void row_epilogue(const StepArgs<T>& a, int64_t row, int64_t c0, T invd, T du,
+                                             const T (&acc)[VEC], const T (&bt)[VEC], const T (&qp)[VEC],
+                                             const T (&qc)[VEC], Acc<T> (&sA)[VEC], Acc<T> (&sB)[VEC],
+                                             Acc<T> (&sC)[VEC])
+{
+    T wv[VEC];
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) wv[i] = invd * acc[i] - bt[i] * qp[i];
+    st_stream<T, VEC>(a.qprev_w + row * a.ld + c0, wv);
+    if (a.do_reduce) {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            const T dw = du * wv[i];
+            sA[i].add(dw * qc[i]);
+            sB[i].add(dw * wv[i]);
+            sC[i].add(dw);
+        }
+    }
+}
+
+// Sum of the heavy row's chunk partials (chunk order, NZL lanes strided).
+template <typename T, int VEC, int NZL>
+__device__ __forceinline__ void heavy_row_sum(const StepArgs<T>& a, int64_t row, int64_t c0, int zl, T (&acc)[VEC])
+{
+    int64_t lo = 0, hi = a.n_heavy_rows - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a.heavy_rows[mid] < row) lo = mid + 1; else hi = mid;
+    }
+    const int f = a.heavy_first[lo], l = a.heavy_first[lo + 1];
+    for (int c = f + zl; c < l; c += NZL) {
+        T x[VEC];
+        ld_plain<T, VEC>(x, a.heavy_part + (int64_t)c * a.ld + c0);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[i] += x[i];
+    }
+}
+
 // Partial sums of each heavy-row chunk: heavy_part[chunk, :] = sum over the chunk's nonzeros.
 template <typename T, int VEC, int GS, int NZL, bool WEIGHTED>
 __global__ void __launch_bounds__(kBlock) k_spmm_heavy(const StepArgs<T> a)
@@ -235,6 +310,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm_heavy(const StepArgs<T> a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cl = lane % GS, zl = (lane / GS) % NZL;
     const int rs = lane / (GS * NZL);
+    const int li = lane % (GS * NZL);
     const unsigned mask = group_mask<GS, NZL>(lane);
     const int64_t nslots = (int64_t)gridDim.x * kWarps * RPW;
     const int64_t slot0 = ((int64_t)blockIdx.x * kWarps + warp) * RPW + rs;
@@ -245,7 +321,8 @@ __global__ void __launch_bounds__(kBlock) k_spmm_heavy(const StepArgs<T> a)
             T acc[VEC];
 #pragma unroll
             for (int i = 0; i < VEC; ++i) acc[i] = T(0);
-            gather_row<T, VEC, NZL, WEIGHTED>(a, (int64_t)a.chunk_beg[ch] + zl, (int64_t)a.chunk_end[ch], c0, acc);
+            gather_row<T, VEC, GS, NZL, kUnroll<T, VEC>, WEIGHTED>(a, (int64_t)a.chunk_beg[ch], (int64_t)a.chunk_end[ch],
+                                                                  c0, li, zl, mask, acc);
             reduce_nzl<GS, NZL>(acc, mask);
             if (zl == 0) st_plain<T, VEC>(a.heavy_part + ch * a.ld + c0, acc);
         }
@@ -264,6 +341,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(const StepArgs<T> a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cl = lane % GS, zl = (lane / GS) % NZL;
     const int rs = lane / (GS * NZL);
+    const int li = lane % (GS * NZL);
     const unsigned mask = group_mask<GS, NZL>(lane);
     const int64_t nslots = (int64_t)gridDim.x * kWarps * RPW;
     const int64_t slot0 = ((int64_t)blockIdx.x * kWarps + warp) * RPW + rs;
@@ -278,73 +356,299 @@ __global__ void __launch_bounds__(kBlock) k_spmm(const StepArgs<T> a)
 
         for (int64_t row = slot0; row < a.n; row += nslots) {
             const int64_t beg = a.row_ptr[row], end = a.row_ptr[row + 1];
-            T acc[VEC];
+            T acc[VEC], qp[VEC], qc[VEC];
 #pragma unroll
             for (int i = 0; i < VEC; ++i) acc[i] = T(0);
-            if (end - beg > a.heavy_thr) {
-                int64_t lo = 0, hi = a.n_heavy_rows - 1;
-                while (lo < hi) {
-                    const int64_t mid = (lo + hi) >> 1;
-                    if (a.heavy_rows[mid] < row) lo = mid + 1; else hi = mid;
-                }
-                const int f = a.heavy_first[lo], l = a.heavy_first[lo + 1];
-                for (int c = f + zl; c < l; c += NZL) {
-                    T x[VEC];
-                    ld_plain<T, VEC>(x, a.heavy_part + (int64_t)c * ld + c0);
-#pragma unroll
-                    for (int i = 0; i < VEC; ++i) acc[i] += x[i];
-                }
-            } else {
-                gather_row<T, VEC, NZL, WEIGHTED>(a, beg + zl, end, c0, acc);
-            }
-            reduce_nzl<GS, NZL>(acc, mask);
-            if (zl == 0) {
-                const T invd = a.invdeg[row];
-                const T du = a.deg[row];
-                T qp[VEC], qc[VEC], wv[VEC];
+            if (zl == 0) {  // own-row operands of the epilogue, issued before the gather
                 ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
                 ld_gather<T, VEC>(qc, a.qcur + row * ld + c0);
+            }
+            if (end - beg > a.heavy_thr) {
+                heavy_row_sum<T, VEC, NZL>(a, row, c0, zl, acc);
+            } else {
+                gather_row<T, VEC, GS, NZL, kUnroll<T, VEC>, WEIGHTED>(a, beg, end, c0, li, zl, mask, acc);
+            }
+            reduce_nzl<GS, NZL>(acc, mask);
+            if (zl == 0) row_epilogue<T, VEC>(a, row, c0, a.invdeg[row], a.deg[row], acc, bt, qp, qc, sA, sB, sC);
+        }
+
+        if (a.do_reduce) block_partials<T, VEC, GS * NZL, TP>(a, sA, sB, sC, red, slab, lane, warp, cl);
+    }
+}
+
+
+// Per-thread accumulators of the three reductions kept in shared memory (column
+// threadIdx.x of a [quantity][VEC][kBlock] array, bank-conflict free); FP32 sums are
+// Kahan-compensated, FP64 sums plain. Used by the row-stream kernel to keep registers
+// for gathers in flight.
+template <typename T, int VEC>
+struct SmemAcc;
+
+template <int VEC>
+struct SmemAcc<float, VEC> {
+    static constexpr int kWords = 3 * VEC * 2;  // floats per thread
+    float* p;
+    __device__ __forceinline__ void init(float* base)
+    {
+        p = base + threadIdx.x;
 #pragma unroll
-                for (int i = 0; i < VEC; ++i) wv[i] = invd * acc[i] - bt[i] * qp[i];
-                st_stream<T, VEC>(a.qprev_w + row * ld + c0, wv);
-                if (a.do_reduce) {
+        for (int k = 0; k < kWords; ++k) p[k * kBlock] = 0.f;
+    }
+    __device__ __forceinline__ void add(int q, int i, float x)
+    {
+        float* sp = p + ((q * VEC + i) * 2) * kBlock;
+        float* cp = sp + kBlock;
+        const float s = *sp, c = *cp;
+        const float y = x - c;
+        const float t = s + y;
+        *cp = (t - s) - y;
+        *sp = t;
+    }
+    __device__ __forceinline__ double value(int q, int i) const
+    {
+        const float* sp = p + ((q * VEC + i) * 2) * kBlock;
+        return (double)sp[0] - (double)sp[kBlock];
+    }
+};
+
+template <int VEC>
+struct SmemAcc<double, VEC> {
+    static constexpr int kWords = 3 * VEC * 2;  // 32-bit words per thread
+    double* p;
+    __device__ __forceinline__ void init(float* base)
+    {
+        p = reinterpret_cast<double*>(base) + threadIdx.x;
 #pragma unroll
-                    for (int i = 0; i < VEC; ++i) {
-                        const T dw = du * wv[i];
-                        sA[i].add(dw * qc[i]);
-                        sB[i].add(dw * wv[i]);
-                        sC[i].add(dw);
+        for (int k = 0; k < 3 * VEC; ++k) p[k * kBlock] = 0.0;
+    }
+    __device__ __forceinline__ void add(int q, int i, double x) { p[(q * VEC + i) * kBlock] += x; }
+    __device__ __forceinline__ double value(int q, int i) const { return p[(q * VEC + i) * kBlock]; }
+};
+
+template <typename T, int VEC, int TP>
+constexpr size_t rows_smem_bytes()
+{
+    return (size_t)SmemAcc<T, VEC>::kWords * 4 * kBlock + (size_t)kWarps * TP * 8;
+}
+
+// Block partials from shared-memory accumulators (same tree as block_partials).
+template <typename T, int VEC, int GW, int TP>
+__device__ __forceinline__ void block_partials_s(const StepArgs<T>& a, const SmemAcc<T, VEC>& acc,
+                                                 double (*red)[TP], int slab, int lane, int warp, int cl)
+{
+#pragma unroll
+    for (int qn = 0; qn < 3; ++qn) {
+        double v[VEC];
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) v[i] = acc.value(qn, i);
+#pragma unroll
+        for (int off = GW; off < 32; off <<= 1) {
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+        }
+        if (lane < TP / VEC) {
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) red[warp][cl * VEC + i] = v[i];
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < TP; c += kBlock) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) sum += red[w][c];
+            a.block_part[(((int64_t)slab * gridDim.x + blockIdx.x) * 3 + qn) * TP + c] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void row_epilogue_s(const StepArgs<T>& a, int64_t row, int64_t c0, T invd, T du,
+                                               const T (&acc)[VEC], const T (&bt)[VEC], const T (&qp)[VEC],
+                                               const T (&qc)[VEC], SmemAcc<T, VEC>& sacc)
+{
+    T wv[VEC];
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) wv[i] = invd * acc[i] - bt[i] * qp[i];
+    st_stream<T, VEC>(a.qprev_w + row * a.ld + c0, wv);
+    if (a.do_reduce) {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            const T dw = du * wv[i];
+            sacc.add(0, i, dw * qc[i]);
+            sacc.add(1, i, dw * wv[i]);
+            sacc.add(2, i, dw);
+        }
+    }
+}
+
+template <typename T, int VEC>
+inline constexpr int kMinBlocks = 2;
+
+// Row-stream variant: a row group of GS lanes (VEC columns each) walks a task -- a
+// contiguous row range holding at most a fixed number of nonzeros, or one heavy row --
+// as a single stream of nonzeros. Column indices come GS at a time in one coalesced
+// load; U gathers per lane are in flight per round and stay in flight across row
+// boundaries; row_ptr, 1/d and d of the task's rows are loaded GS rows at a time and
+// broadcast by shuffle; the epilogue of a row runs when the stream crosses its end.
+template <typename T, int VEC, int GS, bool WEIGHTED>
+__global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const StepArgs<T> a)
+{
+    constexpr int TP = VEC * GS;
+    constexpr int NG = 32 / GS;
+    constexpr int U = kUnroll<T, VEC>;
+    constexpr int CH = GS > U ? GS : U;  // indices per coalesced index load
+    extern __shared__ __align__(16) float smem_f[];
+    double(*red)[TP] = reinterpret_cast<double(*)[TP]>(smem_f + SmemAcc<T, VEC>::kWords * kBlock);
+    if (a.active_prev && *a.active_prev == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % GS, grp = lane / GS;
+    const unsigned mask = group_mask<GS, 1>(lane);
+    const int64_t ngroups = (int64_t)gridDim.x * kWarps * NG;
+    const int64_t gid = ((int64_t)blockIdx.x * kWarps + warp) * NG + grp;
+    const int nslab = (int)(a.ld / TP);
+    const int64_t ld = a.ld;
+    const T* __restrict__ qbase = a.qcur;
+
+    for (int slab = 0; slab < nslab; ++slab) {
+        const int64_t c0 = (int64_t)slab * TP + gl * VEC;
+        T bt[VEC];
+        ld_plain<T, VEC>(bt, a.cf_beta + c0);
+        SmemAcc<T, VEC> sacc;
+        sacc.init(smem_f);
+        const T* __restrict__ q = qbase + c0;
+
+        for (int64_t task = gid; task < a.ntasks; task += ngroups) {
+            const int64_t r0 = a.task_row[task], r1 = a.task_row[task + 1];
+            const int64_t e_beg = a.row_ptr[r0], e_end = a.row_ptr[r1];
+            T acc[VEC], qp[VEC], qc[VEC];
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[i] = T(0);
+            if (r1 == r0 + 1 && e_end - e_beg > a.heavy_thr) {
+                ld_stream<T, VEC>(qp, a.qprev_w + r0 * ld + c0);
+                ld_gather<T, VEC>(qc, q + r0 * ld);
+                heavy_row_sum<T, VEC, 1>(a, r0, c0, 0, acc);
+                row_epilogue_s<T, VEC>(a, r0, c0, a.invdeg[r0], a.deg[r0], acc, bt, qp, qc, sacc);
+                continue;
+            }
+            // row window: lane gl holds row_ptr[w0 + gl + 1], 1/d and d of row w0 + gl
+            int64_t w0 = r0;
+            int64_t my_end = (w0 + gl < r1) ? a.row_ptr[w0 + gl + 1] : e_end;
+            T my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : T(0);
+            T my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : T(0);
+            int64_t row = r0;
+            int64_t row_end = __shfl_sync(mask, my_end, 0, GS);
+            ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
+            ld_gather<T, VEC>(qc, q + row * ld);
+            for (int64_t base = e_beg; base < e_end; base += CH) {
+                const int cnt = (int)(e_end - base < CH ? e_end - base : CH);
+                int my_col[CH / GS];
+                float my_w[CH / GS];
+#pragma unroll
+                for (int h = 0; h < CH / GS; ++h) {
+                    const int idx = h * GS + gl;
+                    my_col[h] = idx < cnt ? __ldg(a.col + base + idx) : 0;
+                    if constexpr (WEIGHTED) my_w[h] = idx < cnt ? __ldg(a.w + base + idx) : 0.0f;
+                }
+                for (int k0 = 0; k0 < cnt; k0 += U) {
+                    T x[U][VEC];
+                    T wu[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        // k0 is a multiple of CH when GS < U (then k0 == 0), and k0 + u < GS otherwise
+                        const int kk = k0 + u;
+                        constexpr int hh_div = GS >= U ? 0 : GS;
+                        const int hh = hh_div ? u / (hh_div ? hh_div : 1) : 0;
+                        const int j = __shfl_sync(mask, my_col[hh], kk % GS, GS);
+                        if constexpr (WEIGHTED) wu[u] = (T)__shfl_sync(mask, my_w[hh], kk % GS, GS);
+                        if (kk < cnt) {
+                            ld_gather<T, VEC>(x[u], q + (int64_t)j * ld);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < VEC; ++i) x[u][i] = T(0);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int64_t e = base + k0 + u;
+                        if (e >= e_end) break;
+                        while (e >= row_end) {  // the stream leaves `row`
+                            const int wi = (int)(row - w0);
+                            const T invd = __shfl_sync(mask, my_invd, wi, GS);
+                            const T du = __shfl_sync(mask, my_deg, wi, GS);
+                            row_epilogue_s<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, sacc);
+#pragma unroll
+                            for (int i = 0; i < VEC; ++i) acc[i] = T(0);
+                            ++row;
+                            if (row - w0 >= GS) {  // refill the row window
+                                w0 = row;
+                                my_end = (w0 + gl < r1) ? a.row_ptr[w0 + gl + 1] : e_end;
+                                my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : T(0);
+                                my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : T(0);
+                            }
+                            row_end = __shfl_sync(mask, my_end, (int)(row - w0), GS);
+                            ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
+                            ld_gather<T, VEC>(qc, q + row * ld);
+                        }
+                        if constexpr (WEIGHTED) {
+#pragma unroll
+                            for (int i = 0; i < VEC; ++i) acc[i] += wu[u] * x[u][i];
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < VEC; ++i) acc[i] += x[u][i];
+                        }
                     }
                 }
             }
-        }
-
-        if (a.do_reduce) {
+            // last row of the task (and any rows without nonzeros after it)
+            while (row < r1) {
+                const int wi = (int)(row - w0);
+                const T invd = __shfl_sync(mask, my_invd, wi, GS);
+                const T du = __shfl_sync(mask, my_deg, wi, GS);
+                row_epilogue_s<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, sacc);
 #pragma unroll
-            for (int qn = 0; qn < 3; ++qn) {
-                double v[VEC];
-#pragma unroll
-                for (int i = 0; i < VEC; ++i) v[i] = qn == 0 ? sA[i].value() : (qn == 1 ? sB[i].value() : sC[i].value());
-#pragma unroll
-                for (int off = GS * NZL; off < 32; off <<= 1) {
-#pragma unroll
-                    for (int i = 0; i < VEC; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+                for (int i = 0; i < VEC; ++i) acc[i] = T(0);
+                ++row;
+                if (row >= r1) break;
+                if (row - w0 >= GS) {
+                    w0 = row;
+                    my_end = (w0 + gl < r1) ? a.row_ptr[w0 + gl + 1] : e_end;
+                    my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : T(0);
+                    my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : T(0);
                 }
-                if (lane < GS) {
-#pragma unroll
-                    for (int i = 0; i < VEC; ++i) red[warp][cl * VEC + i] = v[i];
-                }
-                __syncthreads();
-                for (int c = threadIdx.x; c < TP; c += kBlock) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int w = 0; w < kWarps; ++w) s += red[w][c];
-                    a.block_part[(((int64_t)slab * gridDim.x + blockIdx.x) * 3 + qn) * TP + c] = s;
-                }
-                __syncthreads();
+                ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
+                ld_gather<T, VEC>(qc, q + row * ld);
             }
         }
+        if (a.do_reduce) block_partials_s<T, VEC, GS, TP>(a, sacc, red, slab, lane, warp, gl);
+        __syncthreads();  // accumulators are re-initialised by the next slab
     }
+}
+
+template <typename T, int VEC, int GS>
+bool launch_rows_cfg(bool weighted, int grid, cudaStream_t st, const StepArgs<T>& a)
+{
+    constexpr size_t sm = rows_smem_bytes<T, VEC, VEC * GS>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_spmm_rows<T, VEC, GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_spmm_rows<T, VEC, GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    if (weighted) k_spmm_rows<T, VEC, GS, true><<<grid, kBlock, sm, st>>>(a);
+    else k_spmm_rows<T, VEC, GS, false><<<grid, kBlock, sm, st>>>(a);
+    return true;
+}
+
+template <typename T, int VEC, int GS>
+int occupancy_rows_cfg(bool weighted)
+{
+    int nb = 0;
+    constexpr size_t sm = rows_smem_bytes<T, VEC, VEC * GS>();
+    cudaFuncSetAttribute(k_spmm_rows<T, VEC, GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_spmm_rows<T, VEC, GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_rows<T, VEC, GS, true>, kBlock, sm);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_rows<T, VEC, GS, false>, kBlock, sm);
+    return nb;
 }
 
 template <typename T, int VEC, int GS, int NZL>

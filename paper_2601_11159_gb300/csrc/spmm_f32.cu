@@ -3,6 +3,14 @@
 
 namespace rd {
 
+#define RD_F32_ROWS(X) \
+    X(4, 4) \
+    X(4, 8) \
+    X(4, 16) \
+    X(4, 32) \
+    X(8, 32) \
+    X(1, 1)
+
 #define RD_F32_CONFIGS(X) \
     X(1, 1, 4)            \
     X(1, 1, 8)            \
@@ -20,6 +28,13 @@ namespace rd {
 bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
                      const StepArgs<float>& a)
 {
+    if (c.kind == 1 && !heavy) {
+#define X(V, G) \
+    if (c.vec == V && c.gs == G && c.nzl == 1) return launch_rows_cfg<float, V, G>(weighted, grid, st, a);
+        RD_F32_ROWS(X)
+#undef X
+        return false;
+    }
 #define X(V, G, Z) \
     if (c.vec == V && c.gs == G && c.nzl == Z) return launch_cfg<float, V, G, Z>(weighted, heavy, grid, st, a);
     RD_F32_CONFIGS(X)
@@ -29,6 +44,13 @@ bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
 
 int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy)
 {
+    if (c.kind == 1 && !heavy) {
+#define X(V, G) \
+    if (c.vec == V && c.gs == G && c.nzl == 1) return occupancy_rows_cfg<float, V, G>(weighted);
+        RD_F32_ROWS(X)
+#undef X
+        return 0;
+    }
 #define X(V, G, Z) \
     if (c.vec == V && c.gs == G && c.nzl == Z) return occupancy_cfg<float, V, G, Z>(weighted, heavy);
     RD_F32_CONFIGS(X)
@@ -39,8 +61,11 @@ int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy)
 std::vector<SpmmCfg> spmm_configs_f32()
 {
     std::vector<SpmmCfg> v;
-#define X(V, G, Z) v.push_back(SpmmCfg{V, G, Z});
+#define X(V, G, Z) v.push_back(SpmmCfg{V, G, Z, 0});
     RD_F32_CONFIGS(X)
+#undef X
+#define X(V, G) v.push_back(SpmmCfg{V, G, 1, 1});
+    RD_F32_ROWS(X)
 #undef X
     return v;
 }
