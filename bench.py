@@ -143,10 +143,10 @@ def allmax(world, x: float) -> float:
     return float(t.item())
 
 
-def workload(rank: int):
+def workload(rank: int, n: int = 1_000_000, pairs: int = 256):
     from graphgen import workloads as W
 
-    g, s, t = W.chunglu(1_000_000, 2.1, 20.0, 10_000_000, 256, W.BASE_SEED + 2 + 1000 * rank)
+    g, s, t = W.chunglu(n, 2.1, 20.0, n * 10, pairs, W.BASE_SEED + 2 + 1000 * rank)
     return g, s, t
 
 
@@ -199,6 +199,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32)
     ap.add_argument("--plain-sample", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=1_000_000, help="graph size (smaller only for profiling)")
+    ap.add_argument("--pairs", type=int, default=256)
+    ap.add_argument("--kernel", default="tuned", choices=["tuned", "group", "stream"])
+    ap.add_argument("--rhs-tile", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -214,12 +220,12 @@ def main():
 
     if not os.path.exists(B.LIB):
         B.build()
-    g, s_np, t_np = workload(rank)
+    g, s_np, t_np = workload(rank, args.n, args.pairs)
     P = s_np.size
     G = rd.Graph.from_csr(g)
     s_dev = torch.from_numpy(s_np).cuda()
     t_dev = torch.from_numpy(t_np).cuda()
-    opts = dict(mode="fp32", k_max=K_MAX, rel_tol=REL_TOL)
+    opts = dict(mode="fp32", k_max=K_MAX, rel_tol=REL_TOL, kernel=args.kernel, rhs_tile=args.rhs_tile)
     stream = torch.cuda.current_stream()
 
     # warm-up (also settles the workspace)
@@ -259,6 +265,21 @@ def main():
     status = res.status.cpu().numpy()
 
     # end to end: host (pinned) pair ids in, host results out, copies inside the timed region
+    e2e_value = None
+    plain_value = None
+    plain_r = None
+    if not args.no_e2e:
+        e2e_value = run_e2e(G, s_np, t_np, opts, args, world)
+    if not args.no_plain:
+        plain_value, plain_r = run_plain(G, s_dev, t_dev, opts, args, stream)
+    return finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st, launches, spmm_ms,
+                  spmm_n, spmm_bytes, steps_max, clocks, e2e_value, plain_value, plain_r, s_np, t_np)
+
+
+def run_e2e(G, s_np, t_np, opts, args, world):
+    import torch
+
+    P = s_np.size
     s_h = torch.from_numpy(s_np).pin_memory()
     t_h = torch.from_numpy(t_np).pin_memory()
     for _ in range(2):
@@ -270,10 +291,15 @@ def main():
         re2e = G.query(s_h, t_h, **opts)
     torch.cuda.synchronize()
     e2e_s = allmax(world, time.perf_counter() - t0)
-    e2e_value = P * world * args.steps / e2e_s
     assert isinstance(re2e.r, np.ndarray)
+    return P * world * args.steps / e2e_s
 
-    # plain one-pair-per-launch path on a sample of the same pairs
+
+def run_plain(G, s_dev, t_dev, opts, args, stream):
+    """The plain one-pair-per-launch path on a sample of the same pairs."""
+    import torch
+
+    P = s_dev.numel()
     ps = min(args.plain_sample, P)
     for _ in range(2):
         G.query(s_dev[:2], t_dev[:2], plain=True, **opts)
@@ -284,9 +310,11 @@ def main():
     rp = G.query(s_dev[:ps], t_dev[:ps], plain=True, **opts)
     p1.record(stream)
     torch.cuda.synchronize()
-    plain_value = ps / (p0.elapsed_time(p1) / 1000.0)
-    plain_r = rp.r.cpu().numpy()
+    return ps / (p0.elapsed_time(p1) / 1000.0), rp.r.cpu().numpy()
 
+
+def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st, launches, spmm_ms, spmm_n,
+           spmm_bytes, steps_max, clocks, e2e_value, plain_value, plain_r, s_np, t_np):
     if rank != 0:
         return 0
 
@@ -301,18 +329,20 @@ def main():
         cs = min(args.cpu_sample, P)
         r_or, k_or, used, dt = cpu_oracle(g, s_np, t_np, cs)
         rel = np.abs(r_gpu[:cs] - r_or) / np.abs(r_or)
-        rel_plain = np.abs(plain_r - r_or[:ps]) / np.abs(r_or[:ps])
         max_rel = float(rel.max())
         cpu = {"value": cs / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
                "sample": f"{cs} of the 256 pairs, FP64 C Lanczos, stop at relative increment 1e-9",
-               "max_rel_err_gpu_vs_oracle": max_rel, "max_rel_err_plain_vs_oracle": float(rel_plain.max()),
-               "median_rel_err_gpu_vs_oracle": float(np.median(rel))}
+               "max_rel_err_gpu_vs_oracle": max_rel, "median_rel_err_gpu_vs_oracle": float(np.median(rel))}
+        if plain_r is not None:
+            ps = plain_r.size
+            cpu["max_rel_err_plain_vs_oracle"] = float((np.abs(plain_r - r_or[:ps]) / np.abs(r_or[:ps])).max())
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "chunglu1m_256pairs", "n": g.n, "nnz": g.nnz, "pairs": P,
+        "config": {"workload": "chunglu1m_256pairs" if args.n == 1_000_000 and P == 256 else
+                   f"chunglu{args.n}_{P}pairs", "n": g.n, "nnz": g.nnz, "pairs": P, "kernel": int(st["kernel"]),
                    "precision": "FP32 vectors and SpMM, FP64 alpha/beta/T_k and reductions",
                    "stop": f"estimated relative error <= {REL_TOL}", "k_max": K_MAX,
                    "lanczos_steps_max": int(steps_max), "iters_median": float(np.median(iters)),
@@ -320,15 +350,16 @@ def main():
                    "l2": "inputs larger than L2 (two 1 GB vector blocks per query)",
                    "parallelism": f"replicas x{world}, pairs sharded, no collective",
                    "all_pairs_ok": bool(np.all(status >= 0))},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * 4 * P),
-                "d2h_bytes_per_step": int(24 * P)},
+        "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
+                                               "h2d_bytes_per_step": int(2 * 4 * P),
+                                               "d2h_bytes_per_step": int(24 * P)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "k_spmm (+ k_spmm_heavy)", "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                      "algorithmic_bytes_per_launch": spmm_bytes, "avg_launch_ms": avg_launch_ms},
         "plain_pairs_per_s": plain_value,
-        "batched_over_plain": value / world / plain_value,
+        "batched_over_plain": None if plain_value is None else value / world / plain_value,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "max_rel_err": max_rel,

@@ -30,17 +30,20 @@ def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(HERE, "..", "include", "*.h"))
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, out_dir: str = OUT_DIR, extra_flags=()) -> str:
+    """Compile every csrc/*.cu and link librd.so into ``out_dir`` (extra nvcc flags, e.g. -D
+    tuning macros, go to every translation unit)."""
+    os.makedirs(out_dir, exist_ok=True)
+    lib_path = os.path.join(out_dir, "librd.so")
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = max([os.path.getmtime(h) for h in _headers()] + [0.0])
     procs, objs = [], []
     for src in sources:
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         stale = force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_time)
         if stale:
-            cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
+            cmd = [nvcc()] + ARCH + FLAGS + list(extra_flags) + ["-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -53,12 +56,12 @@ def build(verbose: bool = False, force: bool = False) -> str:
             print(out.decode(errors="replace"), file=sys.stderr)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(f"{s}:\n{o}" for s, o in failed))
-    if force or procs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or procs or not os.path.exists(lib_path):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fPIC"]
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -324,7 +324,7 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     int tp = o.rhs_tile;
     if (tp <= 0) {
         if (fp64) tp = P <= 8 ? 8 : (P <= 16 ? 16 : (P <= 32 ? 32 : 64));
-        else tp = P <= 16 ? 16 : (P <= 32 ? 32 : (P <= 64 ? 64 : 128));
+        else tp = P <= 16 ? 16 : (P <= 32 ? 32 : (P <= 64 ? 64 : (P <= 128 ? 128 : 256)));
     }
     c.vec = fp64 ? (tp >= 128 ? 4 : 2) : (tp >= 256 ? 8 : 4);
     c.gs = std::max(1, tp / c.vec);

@@ -159,8 +159,11 @@ struct Acc<double> {
 };
 
 // Independent gathers in flight per lane per round: 8 for 16-byte lanes, 4 for wider ones.
+#ifndef RD_ROWS_UNROLL
+#define RD_ROWS_UNROLL 8
+#endif
 template <typename T, int VEC>
-inline constexpr int kUnroll = (int)sizeof(T) * VEC > 16 ? 4 : 8;
+inline constexpr int kUnroll = (int)sizeof(T) * VEC > 16 ? (RD_ROWS_UNROLL > 4 ? 4 : RD_ROWS_UNROLL) : RD_ROWS_UNROLL;
 
 // Sum over the nonzeros [beg, end) of w_e * q[col_e, c0 .. c0+VEC), shared by the G = GS*NZL
 // lanes of a row group: the group loads up to G column indices (and weights) with one
@@ -481,15 +484,77 @@ __device__ __forceinline__ void row_epilogue_s(const StepArgs<T>& a, int64_t row
     }
 }
 
+#ifndef RD_ROWS_MINB
+#define RD_ROWS_MINB 2
+#endif
 template <typename T, int VEC>
-inline constexpr int kMinBlocks = 2;
+inline constexpr int kMinBlocks = RD_ROWS_MINB;
+
+#ifndef RD_ROWS_PREFETCH
+#define RD_ROWS_PREFETCH 1  // prefetch each chunk's gathered rows into L1 at the chunk start
+#endif
+#ifndef RD_ROWS_BATCH
+#define RD_ROWS_BATCH 4     // rows whose terms are summed in registers before one Kahan update
+#endif
+
+// Row terms of the three reductions summed over a batch of rows in registers, then added
+// to the Kahan accumulators in shared memory (one compensated update per batch).
+template <typename T, int VEC>
+struct RowBatch {
+    T b[3][VEC];
+    int cnt;
+    __device__ __forceinline__ void reset()
+    {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) b[q][i] = T(0);
+        cnt = 0;
+    }
+    __device__ __forceinline__ void flush(SmemAcc<T, VEC>& acc)
+    {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc.add(q, i, b[q][i]);
+        reset();
+    }
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ void row_epilogue_b(const StepArgs<T>& a, int row, int64_t c0, T invd, T du,
+                                               const T (&acc)[VEC], const T (&bt)[VEC], const T (&qp)[VEC],
+                                               const T (&qc)[VEC], RowBatch<T, VEC>& rb, SmemAcc<T, VEC>& sacc)
+{
+    T wv[VEC];
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) wv[i] = invd * acc[i] - bt[i] * qp[i];
+    st_stream<T, VEC>(a.qprev_w + (int64_t)row * a.ld + c0, wv);
+    if (a.do_reduce) {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            const T dw = du * wv[i];
+            rb.b[0][i] += dw * qc[i];
+            rb.b[1][i] += dw * wv[i];
+            rb.b[2][i] += dw;
+        }
+        if (++rb.cnt == RD_ROWS_BATCH) rb.flush(sacc);
+    }
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 
 // Row-stream variant: a row group of GS lanes (VEC columns each) walks a task -- a
 // contiguous row range holding at most a fixed number of nonzeros, or one heavy row --
-// as a single stream of nonzeros. Column indices come GS at a time in one coalesced
-// load; U gathers per lane are in flight per round and stay in flight across row
-// boundaries; row_ptr, 1/d and d of the task's rows are loaded GS rows at a time and
-// broadcast by shuffle; the epilogue of a row runs when the stream crosses its end.
+// as a single stream of nonzeros. Column indices come CH at a time in one coalesced
+// load, each lane turning its index into a 32-bit offset (in VEC-element units) and
+// optionally prefetching that row's slab into L1; U gathers per lane are in flight per
+// round and stay in flight across row boundaries; row_ptr, 1/d and d of the task's rows
+// are loaded GS rows at a time and broadcast by shuffle; the epilogue of a row runs
+// when the stream crosses its end. Requires n * ld / VEC < 2^32.
 template <typename T, int VEC, int GS, bool WEIGHTED>
 __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const StepArgs<T> a)
 {
@@ -497,17 +562,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
     constexpr int NG = 32 / GS;
     constexpr int U = kUnroll<T, VEC>;
     constexpr int CH = GS > U ? GS : U;  // indices per coalesced index load
+    constexpr int NH = CH / GS;          // indices held per lane
     extern __shared__ __align__(16) float smem_f[];
     double(*red)[TP] = reinterpret_cast<double(*)[TP]>(smem_f + SmemAcc<T, VEC>::kWords * kBlock);
     if (a.active_prev && *a.active_prev == 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = lane % GS, grp = lane / GS;
     const unsigned mask = group_mask<GS, 1>(lane);
-    const int64_t ngroups = (int64_t)gridDim.x * kWarps * NG;
-    const int64_t gid = ((int64_t)blockIdx.x * kWarps + warp) * NG + grp;
+    const int ngroups = gridDim.x * kWarps * NG;
+    const int gid = (blockIdx.x * kWarps + warp) * NG + grp;
     const int nslab = (int)(a.ld / TP);
     const int64_t ld = a.ld;
-    const T* __restrict__ qbase = a.qcur;
+    const uint32_t ldv = (uint32_t)(ld / VEC);  // row stride in VEC-element units
+    const int ntasks = (int)a.ntasks;
 
     for (int slab = 0; slab < nslab; ++slab) {
         const int64_t c0 = (int64_t)slab * TP + gl * VEC;
@@ -515,53 +582,63 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
         ld_plain<T, VEC>(bt, a.cf_beta + c0);
         SmemAcc<T, VEC> sacc;
         sacc.init(smem_f);
-        const T* __restrict__ q = qbase + c0;
+        RowBatch<T, VEC> rb;
+        rb.reset();
+        const T* __restrict__ q = a.qcur + c0;
+        const T* __restrict__ qslab = a.qcur + (int64_t)slab * TP;  // row starts of this slab
 
-        for (int64_t task = gid; task < a.ntasks; task += ngroups) {
-            const int64_t r0 = a.task_row[task], r1 = a.task_row[task + 1];
-            const int64_t e_beg = a.row_ptr[r0], e_end = a.row_ptr[r1];
+        for (int task = gid; task < ntasks; task += ngroups) {
+            const int r0 = a.task_row[task], r1 = a.task_row[task + 1];
+            const int e_beg = (int)a.row_ptr[r0], e_end = (int)a.row_ptr[r1];
             T acc[VEC], qp[VEC], qc[VEC];
 #pragma unroll
             for (int i = 0; i < VEC; ++i) acc[i] = T(0);
             if (r1 == r0 + 1 && e_end - e_beg > a.heavy_thr) {
-                ld_stream<T, VEC>(qp, a.qprev_w + r0 * ld + c0);
-                ld_gather<T, VEC>(qc, q + r0 * ld);
+                ld_stream<T, VEC>(qp, a.qprev_w + (int64_t)r0 * ld + c0);
+                ld_gather<T, VEC>(qc, q + (int64_t)r0 * ld);
                 heavy_row_sum<T, VEC, 1>(a, r0, c0, 0, acc);
-                row_epilogue_s<T, VEC>(a, r0, c0, a.invdeg[r0], a.deg[r0], acc, bt, qp, qc, sacc);
+                row_epilogue_b<T, VEC>(a, r0, c0, a.invdeg[r0], a.deg[r0], acc, bt, qp, qc, rb, sacc);
                 continue;
             }
             // row window: lane gl holds row_ptr[w0 + gl + 1], 1/d and d of row w0 + gl
-            int64_t w0 = r0;
-            int64_t my_end = (w0 + gl < r1) ? a.row_ptr[w0 + gl + 1] : e_end;
+            int w0 = r0;
+            int my_end = (w0 + gl < r1) ? (int)a.row_ptr[w0 + gl + 1] : e_end;
             T my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : T(0);
             T my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : T(0);
-            int64_t row = r0;
-            int64_t row_end = __shfl_sync(mask, my_end, 0, GS);
-            ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
-            ld_gather<T, VEC>(qc, q + row * ld);
-            for (int64_t base = e_beg; base < e_end; base += CH) {
-                const int cnt = (int)(e_end - base < CH ? e_end - base : CH);
-                int my_col[CH / GS];
-                float my_w[CH / GS];
+            int row = r0;
+            int row_end = __shfl_sync(mask, my_end, 0, GS);
+            ld_stream<T, VEC>(qp, a.qprev_w + (int64_t)row * ld + c0);
+            ld_gather<T, VEC>(qc, q + (int64_t)row * ld);
+            for (int base = e_beg; base < e_end; base += CH) {
+                const int cnt = e_end - base < CH ? e_end - base : CH;
+                uint32_t my_off[NH];
+                float my_w[NH];
 #pragma unroll
-                for (int h = 0; h < CH / GS; ++h) {
+                for (int h = 0; h < NH; ++h) {
                     const int idx = h * GS + gl;
-                    my_col[h] = idx < cnt ? __ldg(a.col + base + idx) : 0;
+                    const uint32_t j = idx < cnt ? (uint32_t)__ldg(a.col + base + idx) : 0u;
+                    my_off[h] = j * ldv;
                     if constexpr (WEIGHTED) my_w[h] = idx < cnt ? __ldg(a.w + base + idx) : 0.0f;
+#if RD_ROWS_PREFETCH
+                    if (idx < cnt) {
+                        const char* rowp = reinterpret_cast<const char*>(qslab + (int64_t)j * ld);
+#pragma unroll
+                        for (int L = 0; L < (TP * (int)sizeof(T) + 127) / 128; ++L) prefetch_l1(rowp + 128 * L);
+                    }
+#endif
                 }
                 for (int k0 = 0; k0 < cnt; k0 += U) {
                     T x[U][VEC];
                     T wu[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        // k0 is a multiple of CH when GS < U (then k0 == 0), and k0 + u < GS otherwise
+                        // k0 == 0 when GS < U; otherwise k0 + u < GS
                         const int kk = k0 + u;
-                        constexpr int hh_div = GS >= U ? 0 : GS;
-                        const int hh = hh_div ? u / (hh_div ? hh_div : 1) : 0;
-                        const int j = __shfl_sync(mask, my_col[hh], kk % GS, GS);
+                        const int hh = GS >= U ? 0 : u / (GS >= U ? 1 : GS);
+                        const uint32_t off = __shfl_sync(mask, my_off[hh], kk % GS, GS);
                         if constexpr (WEIGHTED) wu[u] = (T)__shfl_sync(mask, my_w[hh], kk % GS, GS);
                         if (kk < cnt) {
-                            ld_gather<T, VEC>(x[u], q + (int64_t)j * ld);
+                            ld_gather<T, VEC>(x[u], q + (size_t)off * VEC);
                         } else {
 #pragma unroll
                             for (int i = 0; i < VEC; ++i) x[u][i] = T(0);
@@ -569,25 +646,25 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const int64_t e = base + k0 + u;
+                        const int e = base + k0 + u;
                         if (e >= e_end) break;
                         while (e >= row_end) {  // the stream leaves `row`
-                            const int wi = (int)(row - w0);
+                            const int wi = row - w0;
                             const T invd = __shfl_sync(mask, my_invd, wi, GS);
                             const T du = __shfl_sync(mask, my_deg, wi, GS);
-                            row_epilogue_s<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, sacc);
+                            row_epilogue_b<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, rb, sacc);
 #pragma unroll
                             for (int i = 0; i < VEC; ++i) acc[i] = T(0);
                             ++row;
                             if (row - w0 >= GS) {  // refill the row window
                                 w0 = row;
-                                my_end = (w0 + gl < r1) ? a.row_ptr[w0 + gl + 1] : e_end;
+                                my_end = (w0 + gl < r1) ? (int)a.row_ptr[w0 + gl + 1] : e_end;
                                 my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : T(0);
                                 my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : T(0);
                             }
-                            row_end = __shfl_sync(mask, my_end, (int)(row - w0), GS);
-                            ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
-                            ld_gather<T, VEC>(qc, q + row * ld);
+                            row_end = __shfl_sync(mask, my_end, row - w0, GS);
+                            ld_stream<T, VEC>(qp, a.qprev_w + (int64_t)row * ld + c0);
+                            ld_gather<T, VEC>(qc, q + (int64_t)row * ld);
                         }
                         if constexpr (WEIGHTED) {
 #pragma unroll
@@ -601,25 +678,28 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
             }
             // last row of the task (and any rows without nonzeros after it)
             while (row < r1) {
-                const int wi = (int)(row - w0);
+                const int wi = row - w0;
                 const T invd = __shfl_sync(mask, my_invd, wi, GS);
                 const T du = __shfl_sync(mask, my_deg, wi, GS);
-                row_epilogue_s<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, sacc);
+                row_epilogue_b<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, rb, sacc);
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) acc[i] = T(0);
                 ++row;
                 if (row >= r1) break;
                 if (row - w0 >= GS) {
                     w0 = row;
-                    my_end = (w0 + gl < r1) ? a.row_ptr[w0 + gl + 1] : e_end;
+                    my_end = (w0 + gl < r1) ? (int)a.row_ptr[w0 + gl + 1] : e_end;
                     my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : T(0);
                     my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : T(0);
                 }
-                ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
-                ld_gather<T, VEC>(qc, q + row * ld);
+                ld_stream<T, VEC>(qp, a.qprev_w + (int64_t)row * ld + c0);
+                ld_gather<T, VEC>(qc, q + (int64_t)row * ld);
             }
         }
-        if (a.do_reduce) block_partials_s<T, VEC, GS, TP>(a, sacc, red, slab, lane, warp, gl);
+        if (a.do_reduce) {
+            rb.flush(sacc);
+            block_partials_s<T, VEC, GS, TP>(a, sacc, red, slab, lane, warp, gl);
+        }
         __syncthreads();  // accumulators are re-initialised by the next slab
     }
 }

@@ -35,8 +35,11 @@ bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
 #undef X
         return false;
     }
+    // the heavy-row pre-pass of a row-stream config runs the row-group heavy kernel with the
+    // same column tile; single-column tiles use 8 nonzero lanes there
+    const int zl = (c.kind == 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
 #define X(V, G, Z) \
-    if (c.vec == V && c.gs == G && c.nzl == Z) return launch_cfg<float, V, G, Z>(weighted, heavy, grid, st, a);
+    if (c.vec == V && c.gs == G && zl == Z) return launch_cfg<float, V, G, Z>(weighted, heavy, grid, st, a);
     RD_F32_CONFIGS(X)
 #undef X
     return false;
@@ -51,8 +54,9 @@ int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy)
 #undef X
         return 0;
     }
+    const int zl = (c.kind == 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
 #define X(V, G, Z) \
-    if (c.vec == V && c.gs == G && c.nzl == Z) return occupancy_cfg<float, V, G, Z>(weighted, heavy);
+    if (c.vec == V && c.gs == G && zl == Z) return occupancy_cfg<float, V, G, Z>(weighted, heavy);
     RD_F32_CONFIGS(X)
 #undef X
     return 0;
