@@ -178,6 +178,33 @@ rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t 
 rd_status rd_potential(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
                        const rd_query_opts* opts, float* phi_out, double* r_out, void* stream);
 
+/* Batched query without any device allocation -- no counterpart in the paper; it exists
+ * for callers that cannot call cudaMalloc (code running under another framework's
+ * allocator or memory pool, processes that reserve all device memory up front, or
+ * contexts where allocation is forbidden). It runs the same recurrence as rd_query with
+ * the row-group SpMM kernel, taking the graph straight from the caller's device CSR
+ * (no rd_graph is created) and using, as its only scratch, one fixed 32 MiB device
+ * array compiled into this library (every GPU that loads the library holds it until the
+ * process exits).
+ *  n, nnz, row_ptr, col_idx, weights : symmetric CSR as for rd_graph_create, DEVICE pointers;
+ *                    self-loops are rejected (RD_ERR_UNSUPPORTED) since the CSR is used as is.
+ *  s, t            : int32[npairs] device pointers.
+ *  opts            : as rd_query (RD_Q_PROFILE is ignored; the SpMM kernel is always row-group;
+ *                    disconnected pairs are not labelled and end as RD_ERR_NUMERIC).
+ *  r_out           : double[npairs] device pointer; iters_out: int32[npairs] device or NULL.
+ * Limits: the scratch must hold 24*n bytes of degrees plus the query workspace
+ * (2*n*ld vector elements, (k_max+1)*4*ld coefficients, the per-pair state); a request that
+ * does not fit returns RD_ERR_INVALID_ARG with the sizes in rd_last_error() and launches
+ * nothing. Host pointers are rejected with RD_ERR_INVALID_ARG.
+ * Set-up: the first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call before any
+ * stream capture. Sharing: every call uses the same array, which keeps the previous
+ * call's contents (the call clears what must start at zero itself); calls that overlap on
+ * the GPU (other streams, other host threads) race on it. Returns as rd_query. */
+rd_status rd_query_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                           const float* weights, const int32_t* s, const int32_t* t, int64_t npairs,
+                           const rd_query_opts* opts, double* r_out, int32_t* iters_out, void* stream);
+
 /* Statistics of the last call on g (host struct). */
 rd_status rd_last_call_stats(const rd_graph* g, rd_call_stats* out);
 

@@ -28,7 +28,8 @@ from ._lib import (  # noqa: F401
 )
 
 __all__ = ["Graph", "RDError", "query", "edge_grad", "potential", "graph_create", "graph_destroy",
-           "graph_set_weights", "last_call_stats", "status_string", "ResistanceDistance", "lib"]
+           "graph_set_weights", "last_call_stats", "status_string", "ResistanceDistance", "lib",
+           "query_noalloc"]
 
 
 def lib():
@@ -213,6 +214,33 @@ def potential(handle: int, n: int, s, t, stream=None, **kw):
     st = lib().rd_potential(handle, sp, tp_, P, C.byref(o), php, rp, _stream_ptr(stream))
     _check(st, "rd_potential")
     return phi.reshape(P, n), r
+
+
+def query_noalloc(row_ptr, col, w, s, t, stream=None, **kw):
+    """rd_query_noalloc for callers that cannot allocate device memory: every array must be a
+    CUDA tensor (the graph is used in place, no handle is created). Returns (r, iters) as CUDA
+    tensors; the caller may pass ``out=(r, iters)`` to reuse preallocated outputs."""
+    out = kw.pop("out", None)
+    for x in (row_ptr, col, s, t) + (() if w is None else (w,)):
+        if not (_is_torch(x) and x.is_cuda):
+            raise TypeError("query_noalloc takes CUDA tensors only")
+    rp, k1 = _arr(row_ptr, np.int64)
+    cp, k2 = _arr(col, np.int32)
+    wp, k3 = _arr(w, np.float32)
+    sp, ks = _arr(s, np.int32)
+    tp_, kt = _arr(t, np.int32)
+    n = k1.numel() - 1
+    P = ks.numel()
+    if out is None:
+        r, rp_ = _out(True, P, np.float64)
+        it, ip = _out(True, P, np.int32)
+    else:
+        r, it = out
+        rp_, ip = (r.data_ptr() if P else None), (it.data_ptr() if P else None)
+    o = _opts(**kw)
+    st = lib().rd_query_noalloc(n, k2.numel(), rp, cp, wp, sp, tp_, P, C.byref(o), rp_, ip, _stream_ptr(stream))
+    _check(st, "rd_query_noalloc")
+    return r, it
 
 
 # -------------------------------------------------------------------- Graph

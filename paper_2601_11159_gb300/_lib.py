@@ -73,6 +73,7 @@ EXPORTS = [
     "rd_query",
     "rd_edge_grad",
     "rd_potential",
+    "rd_query_noalloc",
     "rd_last_call_stats",
     "rd_status_string",
     "rd_last_error",
@@ -99,6 +100,8 @@ def declare(lib):
     lib.rd_edge_grad.restype = C.c_int
     lib.rd_potential.argtypes = [P, P, P, C.c_int64, C.POINTER(QueryOpts), P, P, P]
     lib.rd_potential.restype = C.c_int
+    lib.rd_query_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, P, P, C.c_int64, C.POINTER(QueryOpts), P, P, P]
+    lib.rd_query_noalloc.restype = C.c_int
     lib.rd_last_call_stats.argtypes = [P, C.POINTER(CallStats)]
     lib.rd_last_call_stats.restype = C.c_int
     lib.rd_status_string.argtypes = [C.c_int]

@@ -147,3 +147,63 @@ rd_status compute_degrees(rd_graph* g, cudaStream_t st)
 }
 
 }  // namespace rd
+
+namespace rd {
+
+// Variants of check_csr / compute_degrees for callers that cannot allocate: the flag
+// block and the per-block degree sums live in caller-provided device scratch, and the
+// block sums come back through a fixed host buffer.
+rd_status check_csr_scratch(rd_graph* g, cudaStream_t st, void* flags_dev, int64_t* self_loops)
+{
+    CheckFlags* f = static_cast<CheckFlags*>(flags_dev);
+    CheckFlags h{};
+    RD_CUDA(cudaMemsetAsync(f, 0, sizeof(CheckFlags), st));
+    k_check_csr<<<grid_for(g->nnz > g->n ? g->nnz : g->n, g->sm_count), 256, 0, st>>>(g->n, g->nnz, g->row_ptr,
+                                                                                       g->col, g->w, f);
+    RD_CUDA(cudaMemcpyAsync(&h, f, sizeof(CheckFlags), cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    if (h.bad_rowptr) {
+        set_error("row_ptr must start at 0, be non-decreasing and end at nnz");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (h.bad_col) {
+        set_error("a column index is outside [0, n)");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (h.bad_weight) {
+        set_error("edge weights must be finite and > 0");
+        return RD_ERR_INVALID_ARG;
+    }
+    k_count_self_loops<<<grid_for(g->n, g->sm_count), 256, 0, st>>>(g->n, g->row_ptr, g->col, f);
+    RD_CUDA(cudaMemcpyAsync(&h, f, sizeof(CheckFlags), cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    *self_loops = (int64_t)h.self_loops;
+    return RD_OK;
+}
+
+int degree_grid(const rd_graph* g) { return grid_for(g->n, g->sm_count); }
+
+rd_status compute_degrees_scratch(rd_graph* g, cudaStream_t st, void* flags_dev, double* block_sums_dev,
+                                  double* block_sums_host)
+{
+    const int grid = grid_for(g->n, g->sm_count);
+    CheckFlags* f = static_cast<CheckFlags*>(flags_dev);
+    CheckFlags h{};
+    RD_CUDA(cudaMemsetAsync(f, 0, sizeof(CheckFlags), st));
+    k_degrees<<<grid, 256, 0, st>>>(g->n, g->row_ptr, g->w, g->deg64, g->invdeg64, g->deg32, g->invdeg32,
+                                    block_sums_dev, f);
+    RD_CUDA(cudaMemcpyAsync(&h, f, sizeof(CheckFlags), cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaMemcpyAsync(block_sums_host, block_sums_dev, sizeof(double) * grid, cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int i = 0; i < grid; ++i) s += block_sums_host[i];
+    g->sumdeg = s;
+    g->mean_deg = g->n ? s / (double)g->n : 0.0;
+    if (h.zero_degree && g->n > 1) {
+        set_error("a vertex has degree 0 (isolated vertex)");
+        return RD_ERR_ZERO_DEGREE;
+    }
+    return RD_OK;
+}
+
+}  // namespace rd

@@ -12,6 +12,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -1106,4 +1108,144 @@ extern "C" rd_status rd_potential(rd_graph* g, const int32_t* s, const int32_t* 
     RD_TRY(finish_outputs(c, r_out, nullptr, nullptr, nullptr, &outs));
     record_stats(c);
     return outs;
+}
+
+// ===================================================== query without allocation
+// rd_query_noalloc: the batched query for callers that must not allocate device memory
+// (code that runs where cudaMalloc is unavailable or forbidden -- inside another
+// framework's memory pool or allocator hooks, or in a process whose device memory is
+// fully reserved up front). All of its scratch lives in one fixed, file-scope device
+// array; the graph is the caller's device CSR, used in place.
+namespace rd {
+
+rd_status check_csr_scratch(rd_graph* g, cudaStream_t st, void* flags_dev, int64_t* self_loops);
+rd_status compute_degrees_scratch(rd_graph* g, cudaStream_t st, void* flags_dev, double* block_sums_dev,
+                                  double* block_sums_host);
+int degree_grid(const rd_graph* g);
+
+// 32 MiB of scratch, held by every GPU that loads this library until the process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 256;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kNoAllocMaxDevices];
+
+// Device address of the scratch array on device `dev` (the current device). In host code
+// the array's name only stands in for the symbol; the address comes from
+// cudaGetSymbolAddress, fetched once per device on that device's first call.
+static rd_status noalloc_scratch_address(int dev, void** out)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("device ordinal out of range for the no-allocation scratch table");
+        return RD_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                       "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return RD_OK;
+}
+
+}  // namespace rd
+
+extern "C" rd_status rd_query_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                      const float* weights, const int32_t* s, const int32_t* t, int64_t npairs,
+                                      const rd_query_opts* opts, double* r_out, int32_t* iters_out, void* stream)
+{
+    g_last_error.clear();
+    if (n < 1 || n >= (1ll << 31) || nnz < 0 || nnz >= (1ll << 31) || npairs < 0) {
+        set_error("need 1 <= n < 2^31, 0 <= nnz < 2^31 and npairs >= 0");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (!row_ptr || (nnz > 0 && !col_idx) || (npairs > 0 && (!s || !t || !r_out))) {
+        set_error("row_ptr, col_idx, s, t and r_out must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    const void* need_dev[] = {row_ptr, nnz > 0 ? col_idx : nullptr, weights, npairs > 0 ? s : nullptr,
+                              npairs > 0 ? t : nullptr, npairs > 0 ? r_out : nullptr,
+                              npairs > 0 ? iters_out : nullptr};
+    for (const void* p : need_dev)
+        if (p && !is_device_ptr(p)) {
+            set_error("rd_query_noalloc takes device pointers only");
+            return RD_ERR_INVALID_ARG;
+        }
+    rd_graph g;
+    if (cudaGetDevice(&g.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g.sm_count, cudaDevAttrMultiProcessorCount, g.device) != cudaSuccess) {
+        rd_status st = cuda_status(cudaGetLastError(), "cudaGetDevice");
+        return st == RD_OK ? RD_ERR_CUDA : st;
+    }
+    g.n = n;
+    g.nnz = g.nnz_in = nnz;
+    g.weighted = weights != nullptr;
+    g.row_ptr = const_cast<int64_t*>(row_ptr);
+    g.col = const_cast<int32_t*>(col_idx);
+    g.w = const_cast<float*>(weights);
+    g.heavy_thr = INT32_MAX;  // no heavy-row chunk lists: the row-group kernel takes every row whole
+    static thread_local int host_poll[16];
+    static thread_local double host_block_sums[1 << 14];
+    g.h_pinned = host_poll;
+
+    rd_query_opts o;
+    RD_TRY(validate_common(&g, s, t, npairs, opts, &o));
+    o.flags &= ~RD_Q_PROFILE;  // no event objects
+    o.kernel = 1;              // row-group kernel: needs no task list
+    if (npairs == 0) return RD_OK;
+
+    void* base = nullptr;
+    RD_TRY(noalloc_scratch_address(g.device, &base));
+    // graph-derived arrays first, then the query workspace (same layout as rd_query's)
+    Carver cg(base);
+    void* flags_dev = cg.take<char>(64);
+    double* bsum = cg.take<double>(1 << 14);
+    g.deg64 = cg.take<double>(n);
+    g.invdeg64 = cg.take<double>(n);
+    g.deg32 = cg.take<float>(n);
+    g.invdeg32 = cg.take<float>(n);
+    const size_t graph_bytes = (cg.off + 255) & ~size_t(255);
+    if (degree_grid(&g) > (1 << 14)) {
+        set_error("too many SMs for the no-allocation degree buffer");
+        return RD_ERR_UNSUPPORTED;
+    }
+    const bool plain = (o.flags & RD_Q_PLAIN) != 0;
+    Plan pl;
+    RD_TRY(make_plan(&g, plain ? 1 : npairs, o, plain, &pl));
+    Buffers tmp;
+    Carver dry(nullptr);
+    const size_t query_bytes = carve(dry, &g, pl, plain ? 1 : npairs, false, &tmp);
+    if (graph_bytes + query_bytes > kNoAllocScratchBytes) {
+        set_error("rd_query_noalloc needs " + std::to_string(graph_bytes + query_bytes) +
+                  " bytes of scratch for this graph, pair count and k_max; its fixed scratch holds " +
+                  std::to_string(kNoAllocScratchBytes) + " bytes (use rd_graph_create/rd_query instead)");
+        return RD_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t loops = 0;
+    RD_TRY(check_csr_scratch(&g, st, flags_dev, &loops));
+    if (loops > 0) {
+        set_error("the CSR holds self-loops; rd_query_noalloc cannot rebuild it (use rd_graph_create)");
+        return RD_ERR_UNSUPPORTED;
+    }
+    RD_TRY(compute_degrees_scratch(&g, st, flags_dev, bsum, host_block_sums));
+    g.ws.base = static_cast<char*>(base) + graph_bytes;
+    g.ws.bytes = kNoAllocScratchBytes - graph_bytes;  // >= query_bytes, so nothing is allocated
+    EventPool ev;
+    rd_status call = RD_OK;
+    if (plain) {
+        for (int64_t p = 0; p < npairs; ++p) {
+            rd_status one = RD_OK;
+            RD_TRY(query_batch(&g, s + p, t + p, 1, o, true, r_out + p, iters_out ? iters_out + p : nullptr,
+                               nullptr, nullptr, st, &one, &ev));
+            if (one == RD_WARN_NOT_CONVERGED) call = one;
+        }
+        return call;
+    }
+    RD_TRY(query_batch(&g, s, t, npairs, o, false, r_out, iters_out, nullptr, nullptr, st, &call, &ev));
+    return call;
 }
