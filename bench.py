@@ -244,6 +244,7 @@ def main():
     spmm_n = 0
     spmm_bytes = 0.0
     steps_max = 0
+    compactions = 0
     e0.record(stream)
     for _ in range(args.steps):
         res = G.query(s_dev, t_dev, profile=True, **opts)
@@ -251,8 +252,9 @@ def main():
         launches += st["launches"]
         spmm_ms += st["spmm_ms"]
         spmm_n += st["spmm_launches"]
-        spmm_bytes = st["spmm_bytes"]
+        spmm_bytes += st["spmm_bytes"]
         steps_max = max(steps_max, st["steps"])
+        compactions += st["compactions"]
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -272,6 +274,7 @@ def main():
         e2e_value = run_e2e(G, s_np, t_np, opts, args, world)
     if not args.no_plain:
         plain_value, plain_r = run_plain(G, s_dev, t_dev, opts, args, stream)
+    st["compactions_per_query"] = compactions / args.steps
     return finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st, launches, spmm_ms,
                   spmm_n, spmm_bytes, steps_max, clocks, e2e_value, plain_value, plain_r, s_np, t_np)
 
@@ -319,8 +322,9 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
         return 0
 
     peak, peak_kind = load_peaks()
+    # SpMM launches shrink as converged pairs are packed: total algorithmic bytes over total time
     avg_launch_ms = spmm_ms / max(spmm_n, 1)
-    achieved = spmm_bytes / (avg_launch_ms / 1000.0) / 1e9 if spmm_n else None
+    achieved = spmm_bytes / (spmm_ms / 1000.0) / 1e9 if spmm_n and spmm_ms > 0 else None
     traffic = load_traffic()
 
     cpu = None
@@ -347,6 +351,7 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
                    "stop": f"estimated relative error <= {REL_TOL}", "k_max": K_MAX,
                    "lanczos_steps_max": int(steps_max), "iters_median": float(np.median(iters)),
                    "rhs_tile": int(st["rhs_tile"]), "rows_per_warp": int(st["rows_per_warp"]),
+                   "compactions_per_query": st["compactions_per_query"],
                    "l2": "inputs larger than L2 (two 1 GB vector blocks per query)",
                    "parallelism": f"replicas x{world}, pairs sharded, no collective",
                    "all_pairs_ok": bool(np.all(status >= 0))},
@@ -357,7 +362,8 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "k_spmm (+ k_spmm_heavy)", "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                     "algorithmic_bytes_per_launch": spmm_bytes, "avg_launch_ms": avg_launch_ms},
+                     "algorithmic_bytes_per_launch": spmm_bytes / max(spmm_n, 1), "avg_launch_ms": avg_launch_ms,
+                     "launches_timed": spmm_n},
         "plain_pairs_per_s": plain_value,
         "batched_over_plain": None if plain_value is None else value / world / plain_value,
         "cpu_baseline": cpu,

@@ -76,6 +76,8 @@ typedef enum {
 #define RD_Q_NO_DEFLATE 2u  /* do not remove the component along D^{1/2}1 from each new vector */
 #define RD_Q_PLAIN 4u       /* answer the pairs one at a time with the single-vector SpMV path */
 #define RD_Q_PROFILE 8u     /* time the dominant kernel with CUDA events (see rd_last_call_stats) */
+#define RD_Q_NO_COMPACT 16u /* rd_query: keep every pair's column until the end instead of packing
+                               the still-active pairs into a narrower block as pairs converge */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */
@@ -85,7 +87,9 @@ typedef struct {
     int32_t mode;          /* rd_mode */
     int32_t rhs_tile;      /* right-hand-side columns per SpMM sweep; 0 = tuned */
     int32_t rows_per_warp; /* rows a warp works on at once; 0 = tuned */
-    int32_t chunk_steps;   /* steps between host convergence polls; 0 = default (8) */
+    int32_t chunk_steps;   /* steps between synchronous host convergence polls where those are used
+                              (rd_edge_grad, rd_potential, rd_query_noalloc); 0 = default (8).
+                              rd_query polls every step, one step behind the device. */
     uint32_t flags;        /* RD_Q_* */
     int32_t kernel;        /* SpMM kernel: 0 = tuned, 1 = row-group (warp lanes split a row's
                               nonzeros), 2 = row-stream (row groups walk runs of consecutive rows) */
@@ -102,8 +106,10 @@ typedef struct {
     int32_t nnz_lanes;       /* lanes that share one row's nonzeros */
     int32_t kernel;          /* SpMM kernel used (1 = row-group, 2 = row-stream) */
     int64_t ld;              /* padded number of right-hand-side columns (vector row stride) */
-    double spmm_bytes;       /* algorithmic bytes of one SpMM launch: 4*nnz (+4*nnz weights)
-                                + 8*(n+1) + 3*ld*n*sizeof(element) */
+    double spmm_bytes;       /* algorithmic bytes of all SpMM launches of the call, each
+                                4*nnz (+4*nnz weights) + 8*(n+1) + 3*ld*n*sizeof(element) with the
+                                ld in force at that launch (it shrinks as converged pairs are packed) */
+    int32_t compactions;     /* times the active pairs were packed into a narrower block */
 } rd_call_stats;
 
 /* Fill `opts` with defaults: k_max 1000, rel_tol 1e-7, resid_tol 0, FP32 vectors with FP64

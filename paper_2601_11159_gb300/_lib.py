@@ -33,6 +33,7 @@ RD_Q_FIXED_K = 1
 RD_Q_NO_DEFLATE = 2
 RD_Q_PLAIN = 4
 RD_Q_PROFILE = 8
+RD_Q_NO_COMPACT = 16
 
 
 class QueryOpts(C.Structure):
@@ -61,6 +62,7 @@ class CallStats(C.Structure):
         ("kernel", C.c_int32),
         ("ld", C.c_int64),
         ("spmm_bytes", C.c_double),
+        ("compactions", C.c_int32),
     ]
 
 

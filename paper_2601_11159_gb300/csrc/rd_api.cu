@@ -369,10 +369,15 @@ static rd_status make_plan(rd_graph* g, int64_t P, const rd_query_opts& o, bool 
 
 // ---------------------------------------------------------- workspace map
 struct Buffers {
-    void* q[2];
+    void* q[2];               // current q_{i-1}/W (slot 0) and q_i (slot 1)
+    void* region_a;           // the two n x ld0 blocks q[] start in
+    void* region_x;           // n x ld0 elements: target of a column compaction (NULL if off)
     void* heavy_part;
     double* block_part;
-    void* cf_hist;
+    void* cf_hist;            // [k_max+1][4][ld0] (fixed layout: gradient, potential, no-alloc)
+    void* cf_cur[2];          // [4][ld0] current coefficients by slot (compacting query)
+    int32_t* slot_pair[2];    // [ld0] slot -> pair after a compaction
+    int32_t* old_slot;        // [ld0] scratch of the compaction
     PairState st;
     int32_t* s;
     int32_t* t;
@@ -391,16 +396,25 @@ struct Buffers {
     size_t state_bytes_begin, state_bytes_end;  // offsets of the region zeroed per query
 };
 
-static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, bool grad, Buffers* b)
+static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, bool grad, Buffers* b,
+                    bool compact = false)
 {
     const int64_t ld = pl.ld, n = g->n, K = pl.k_max;
-    b->q[0] = c.take<char>(n * ld * pl.elem);
-    b->q[1] = c.take<char>(n * ld * pl.elem);
+    b->region_a = c.take<char>(2 * n * ld * pl.elem);
+    b->q[0] = b->region_a;
+    b->q[1] = static_cast<char*>(b->region_a) + n * ld * pl.elem;
+    b->region_x = compact ? c.take<char>(n * ld * pl.elem) : nullptr;
     b->heavy_part = c.take<char>(std::max<int64_t>(g->n_chunks, 1) * ld * pl.elem);
-    b->block_part = c.take<double>((size_t)pl.nslab * pl.grid_main * 3 * pl.cfg.tp());
+    // sized for any column tile and any grid of up to 8 blocks of kBlock threads per SM
+    b->block_part = c.take<double>((size_t)ld * 3 * (size_t)std::max(pl.grid_main, g->sm_count * 8));
+    b->old_slot = c.take<int32_t>(ld);
+    b->slot_pair[0] = c.take<int32_t>(ld);
+    b->slot_pair[1] = c.take<int32_t>(ld);
     c.off = (c.off + 255) & ~size_t(255);
     b->state_bytes_begin = c.off;
-    b->cf_hist = c.take<char>((K + 1) * 4 * ld * pl.elem);
+    b->cf_hist = compact ? nullptr : c.take<char>((K + 1) * 4 * ld * pl.elem);
+    b->cf_cur[0] = compact ? c.take<char>(4 * ld * pl.elem) : nullptr;
+    b->cf_cur[1] = compact ? c.take<char>(4 * ld * pl.elem) : nullptr;
     PairState& s = b->st;
     s.b2 = c.take<double>(ld);
     s.delta = c.take<double>(ld);
@@ -448,7 +462,7 @@ struct EventPool {
     {
         if (used == ev.size()) {
             cudaEvent_t e;
-            cudaEventCreate(&e);
+            cudaEventCreateWithFlags(&e, cudaEventDefault);
             ev.push_back(e);
         }
         return ev[used++];
@@ -462,17 +476,38 @@ struct EventPool {
 // --------------------------------------------------------------- one run
 struct RunCtx {
     rd_graph* g;
-    Plan pl;
+    Plan pl;                // plan the workspace was carved for (ld0 = pl.ld)
+    Plan cur;               // plan in force (narrower after a column compaction)
     Buffers b;
     rd_query_opts o;
     cudaStream_t st;
     int64_t P;
     int steps = 0;          // steps enqueued
     int64_t launches = 0, spmm_launches = 0;
+    double spmm_bytes = 0.0;
     bool profile = false;
+    bool compact = false;   // coefficients by slot in cf_cur, columns packed as pairs finish
+    bool lagged_polls = false;
+    int cf_sel = 0, slot_sel = -1;  // slot_sel < 0: identity slot map
+    bool in_region_x = false;
+    int compactions = 0;
     EventPool* ev = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
 };
+
+static double spmm_launch_bytes(const rd_graph* g, const Plan& p)
+{
+    const double nnz = (double)g->nnz;
+    return 4.0 * nnz + (g->weighted ? 4.0 * nnz : 0.0) + 8.0 * (double)(g->n + 1) +
+           3.0 * (double)p.ld * (double)g->n * (double)p.elem;
+}
+
+template <typename T>
+static const T* coef_block(RunCtx& c, int j)
+{
+    if (c.compact) return static_cast<const T*>(c.b.cf_cur[c.cf_sel]);
+    return static_cast<const T*>(c.b.cf_hist) + (int64_t)j * 4 * c.cur.ld;
+}
 
 template <typename T>
 static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
@@ -480,7 +515,7 @@ static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
     rd_graph* g = c.g;
     StepArgs<T> a{};
     a.n = g->n;
-    a.ld = c.pl.ld;
+    a.ld = c.cur.ld;
     a.row_ptr = g->row_ptr;
     a.col = g->col;
     a.w = g->w;
@@ -493,7 +528,7 @@ static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
     }
     a.qcur = static_cast<const T*>(c.b.q[1]);
     a.qprev_w = static_cast<T*>(c.b.q[0]);
-    a.cf_beta = static_cast<const T*>(c.b.cf_hist) + (int64_t)j * 4 * c.pl.ld;
+    a.cf_beta = coef_block<T>(c, j);
     a.heavy_thr = g->heavy_thr;
     a.n_heavy_rows = g->n_heavy_rows;
     a.n_chunks = g->n_chunks;
@@ -522,20 +557,21 @@ static rd_status enqueue_spmm(RunCtx& c, int j, bool reduce)
     }
     const bool fp64 = sizeof(T) == 8;
     if (c.g->n_chunks > 0) {
-        bool ok = fp64 ? launch_spmm_f64(c.pl.cfg, c.g->weighted, true, c.pl.grid_heavy, c.st,
+        bool ok = fp64 ? launch_spmm_f64(c.cur.cfg, c.g->weighted, true, c.cur.grid_heavy, c.st,
                                          *reinterpret_cast<StepArgs<double>*>(&a))
-                       : launch_spmm_f32(c.pl.cfg, c.g->weighted, true, c.pl.grid_heavy, c.st,
+                       : launch_spmm_f32(c.cur.cfg, c.g->weighted, true, c.cur.grid_heavy, c.st,
                                          *reinterpret_cast<StepArgs<float>*>(&a));
         if (!ok) return RD_ERR_UNSUPPORTED;
         ++c.launches;
     }
-    bool ok = fp64 ? launch_spmm_f64(c.pl.cfg, c.g->weighted, false, c.pl.grid_main, c.st,
+    bool ok = fp64 ? launch_spmm_f64(c.cur.cfg, c.g->weighted, false, c.cur.grid_main, c.st,
                                      *reinterpret_cast<StepArgs<double>*>(&a))
-                   : launch_spmm_f32(c.pl.cfg, c.g->weighted, false, c.pl.grid_main, c.st,
+                   : launch_spmm_f32(c.cur.cfg, c.g->weighted, false, c.cur.grid_main, c.st,
                                      *reinterpret_cast<StepArgs<float>*>(&a));
     if (!ok) return RD_ERR_UNSUPPORTED;
     ++c.launches;
     ++c.spmm_launches;
+    c.spmm_bytes += spmm_launch_bytes(c.g, c.cur);
     if (c.profile) {
         cudaEventRecord(e1, c.st);
         c.spmm_ev.emplace_back(e0, e1);
@@ -548,26 +584,26 @@ static void enqueue_normalize(RunCtx& c, int j, bool with_phi)
 {
     NormArgs<T> a{};
     a.n = c.g->n;
-    a.ld = c.pl.ld;
+    a.ld = c.cur.ld;
     a.w_to_qnext = static_cast<T*>(c.b.q[0]);
     a.qcur = static_cast<const T*>(c.b.q[1]);
-    a.cf = static_cast<const T*>(c.b.cf_hist) + (int64_t)j * 4 * c.pl.ld;
+    a.cf = coef_block<T>(c, j);
     a.phi = with_phi ? static_cast<T*>(c.b.phi) : nullptr;
-    a.coef = with_phi ? static_cast<const T*>(c.b.coef_hist) + (int64_t)j * c.pl.ld : nullptr;
+    a.coef = with_phi ? static_cast<const T*>(c.b.coef_hist) + (int64_t)j * c.cur.ld : nullptr;
     a.active_prev = with_phi ? nullptr : c.b.st.act_count + j;
-    if constexpr (sizeof(T) == 8) launch_normalize_f64(c.pl.grid_norm, c.st, a);
-    else launch_normalize_f32(c.pl.grid_norm, c.st, a);
+    if constexpr (sizeof(T) == 8) launch_normalize_f64(c.cur.grid_norm, c.st, a);
+    else launch_normalize_f32(c.cur.grid_norm, c.st, a);
     ++c.launches;
 }
 
 static void enqueue_init(RunCtx& c, bool replay)
 {
-    const int64_t vbytes = c.g->n * c.pl.ld * (int64_t)c.pl.elem;
+    const int64_t vbytes = c.g->n * c.cur.ld * (int64_t)c.cur.elem;
     cudaMemsetAsync(c.b.q[0], 0, vbytes, c.st);
     cudaMemsetAsync(c.b.q[1], 0, vbytes, c.st);
     InitArgs a{};
     a.n = c.g->n;
-    a.ld = c.pl.ld;
+    a.ld = c.cur.ld;
     a.npairs = (int)c.P;
     a.k_max = c.pl.k_max;
     a.elem_size = (int)c.pl.elem;
@@ -587,16 +623,65 @@ static void enqueue_init(RunCtx& c, bool replay)
     c.launches += 1;
 }
 
+// Pack the columns of the still-active pairs into a block of ld_new columns (ld_new holds
+// at least `active_upper` slots, an upper bound on the active count read one step ago).
+template <typename T>
+static rd_status enqueue_compaction(RunCtx& c, int active_upper)
+{
+    Plan np;
+    rd_query_opts o2 = c.o;
+    o2.rhs_tile = 0;
+    RD_TRY(make_plan(c.g, active_upper, o2, false, &np));
+    if (np.ld >= c.cur.ld) return RD_OK;
+    const int64_t n = c.g->n;
+    void* dst0;
+    void* dst1;
+    if (c.in_region_x) {
+        dst0 = c.b.region_a;
+    } else {
+        dst0 = c.b.region_x;
+    }
+    dst1 = static_cast<char*>(dst0) + n * np.ld * (int64_t)np.elem;
+    CompactArgs a{};
+    a.n = n;
+    a.ld_old = c.cur.ld;
+    a.ld_new = np.ld;
+    a.slot_pair_old = c.slot_sel >= 0 ? c.b.slot_pair[c.slot_sel] : nullptr;
+    a.npairs = (int)c.P;
+    const int new_sel = c.slot_sel == 0 ? 1 : 0;
+    a.slot_pair_new = c.b.slot_pair[new_sel];
+    a.old_slot = c.b.old_slot;
+    a.active = c.b.st.active;
+    a.cf_old = c.b.cf_cur[c.cf_sel];
+    a.cf_new = c.b.cf_cur[1 - c.cf_sel];
+    a.q_src0 = c.b.q[0];
+    a.q_src1 = c.b.q[1];
+    a.q_dst0 = dst0;
+    a.q_dst1 = dst1;
+    a.elem_size = (int)np.elem;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c.g->sm_count * 8,
+                                                                 (n * np.ld + 255) / 256));
+    launch_compact(c.st, grid, a);
+    c.launches += 2;
+    c.b.q[0] = dst0;
+    c.b.q[1] = dst1;
+    c.in_region_x = !c.in_region_x;
+    c.slot_sel = new_sel;
+    c.cf_sel = 1 - c.cf_sel;
+    c.cur = np;
+    ++c.compactions;
+    return RD_OK;
+}
+
 template <typename T>
 static rd_status run_forward(RunCtx& c)
 {
+    c.cur = c.pl;
     enqueue_init(c, false);
     const int chunk = c.o.chunk_steps > 0 ? c.o.chunk_steps : 8;
     FinArgs fa{};
-    fa.ld = c.pl.ld;
     fa.npairs = (int)c.P;
-    fa.tp = c.pl.cfg.tp();
-    fa.nblocks = c.pl.grid_main;
+    fa.pstride = c.pl.ld;
     fa.k_max = c.pl.k_max;
     fa.deflate = (c.o.flags & RD_Q_NO_DEFLATE) ? 0 : 1;
     fa.fixed_k = (c.o.flags & RD_Q_FIXED_K) ? 1 : 0;
@@ -606,7 +691,6 @@ static rd_status run_forward(RunCtx& c)
     fa.sumdeg = c.g->sumdeg;
     fa.block_part = c.b.block_part;
     fa.st = c.b.st;
-    fa.cf_hist = c.b.cf_hist;
     fa.elem_size = (int)c.pl.elem;
     int* h = c.g->h_pinned;
     // first poll: ids valid and at least one active pair
@@ -618,15 +702,48 @@ static rd_status run_forward(RunCtx& c)
         return RD_ERR_INVALID_ARG;
     }
     if (h[1] == 0) return RD_OK;
+    constexpr int kSlots = 4;   // pinned poll slots h[4 .. 7]
+    cudaEvent_t poll_ev[kSlots] = {};
+    if (c.lagged_polls)
+        for (int i = 0; i < kSlots; ++i) poll_ev[i] = c.ev->get();
+    int last_known = h[1];
     for (int j = 0; j < c.pl.k_max; ++j) {
         RD_TRY(enqueue_spmm<T>(c, j, true));
         fa.step = j;
+        fa.ld = c.cur.ld;
+        fa.tp = c.cur.cfg.tp();
+        fa.nblocks = c.cur.grid_main;
+        if (c.compact) {
+            fa.slot_pair = c.slot_sel >= 0 ? c.b.slot_pair[c.slot_sel] : nullptr;
+            fa.cf_step = c.b.cf_cur[c.cf_sel];
+            fa.cf_next = c.b.cf_cur[c.cf_sel];
+        } else {
+            fa.slot_pair = nullptr;
+            fa.cf_step = static_cast<T*>(c.b.cf_hist) + (int64_t)j * 4 * c.cur.ld;
+            fa.cf_next = static_cast<T*>(c.b.cf_hist) + (int64_t)(j + 1) * 4 * c.cur.ld;
+        }
         launch_finalize(c.st, fa);
         ++c.launches;
         enqueue_normalize<T>(c, j, false);
         std::swap(c.b.q[0], c.b.q[1]);
         c.steps = j + 1;
-        if ((j + 1) % chunk == 0 && j + 1 < c.pl.k_max) {
+        if (j + 1 >= c.pl.k_max) break;
+        if (c.lagged_polls) {
+            // count of active pairs after step j lands in h[4 + j % kSlots]; read the count
+            // of the previous step, whose copy has usually completed while step j runs
+            const int sl = j % kSlots;
+            RD_CUDA(cudaMemcpyAsync(h + 4 + sl, c.b.st.act_count + j + 1, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    c.st));
+            RD_CUDA(cudaEventRecord(poll_ev[sl], c.st));
+            if (j >= 1) {
+                const int ps = (j - 1) % kSlots;
+                RD_CUDA(cudaEventSynchronize(poll_ev[ps]));
+                last_known = h[4 + ps];
+                if (last_known == 0) break;  // steps enqueued since return at once
+                if (c.compact && last_known * 2 <= c.cur.ld && c.cur.ld > 16)
+                    RD_TRY(enqueue_compaction<T>(c, last_known));
+            }
+        } else if ((j + 1) % chunk == 0) {
             RD_CUDA(cudaMemcpyAsync(h, c.b.st.act_count + j + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
             RD_CUDA(cudaStreamSynchronize(c.st));
             if (h[0] == 0) break;
@@ -680,9 +797,8 @@ static void record_stats(RunCtx& c)
     s.nnz_lanes = c.pl.cfg.nzl;
     s.kernel = c.pl.cfg.kind == 1 ? 2 : 1;
     s.ld = c.pl.ld;
-    const double nnz = (double)c.g->nnz;
-    s.spmm_bytes = 4.0 * nnz + (c.g->weighted ? 4.0 * nnz : 0.0) + 8.0 * (double)(c.g->n + 1) +
-                   3.0 * (double)c.pl.ld * (double)c.g->n * (double)c.pl.elem;
+    s.spmm_bytes += c.spmm_bytes;
+    s.compactions += c.compactions;
     if (c.profile) {
         double ms = 0.0;
         for (auto& pr : c.spmm_ev) {
@@ -737,30 +853,34 @@ static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t
 }
 
 static rd_status prepare_run(RunCtx& c, rd_graph* g, int64_t P, const rd_query_opts& o, bool plain, bool grad,
-                             cudaStream_t st)
+                             cudaStream_t st, bool compact = false, bool lagged_polls = false)
 {
     c.g = g;
     c.o = o;
     c.st = st;
     c.P = P;
     c.profile = (o.flags & RD_Q_PROFILE) != 0;
+    c.compact = compact;
+    c.lagged_polls = lagged_polls && c.ev != nullptr;
     RD_TRY(make_plan(g, P, o, plain, &c.pl));
+    c.cur = c.pl;
     Carver dry(nullptr);
-    const size_t bytes = carve(dry, g, c.pl, P, grad, &c.b);
+    const size_t bytes = carve(dry, g, c.pl, P, grad, &c.b, compact);
     RD_TRY(ensure_ws(g, bytes));
     Carver real(g->ws.base);
-    carve(real, g, c.pl, P, grad, &c.b);
+    carve(real, g, c.pl, P, grad, &c.b, compact);
     return RD_OK;
 }
 
 // Host-side query of a batch of pairs (all device work on st).
 static rd_status query_batch(rd_graph* g, const int32_t* s, const int32_t* t, int64_t P, const rd_query_opts& o,
                              bool plain, double* r_out, int32_t* iters_out, double* err_out, int32_t* status_out,
-                             cudaStream_t st, rd_status* call_status, EventPool* ev)
+                             cudaStream_t st, rd_status* call_status, EventPool* ev, bool compact = false,
+                             bool lagged_polls = false)
 {
     RunCtx c;
     c.ev = ev;
-    RD_TRY(prepare_run(c, g, P, o, plain, false, st));
+    RD_TRY(prepare_run(c, g, P, o, plain, false, st, compact && !plain, lagged_polls));
     RD_TRY(stage_pairs(c, s, t));
     rd_status rs = o.mode == RD_MODE_FP64 ? run_forward<double>(c) : run_forward<float>(c);
     if (rs < 0) return rs;
@@ -773,6 +893,7 @@ template <typename T>
 static rd_status run_replay(RunCtx& c, int K)
 {
     // Replay of the forward recurrence with the stored coefficients; phi += coef_j q_j.
+    c.cur = c.pl;
     const int64_t vbytes = c.g->n * c.pl.ld * (int64_t)c.pl.elem;
     RD_CUDA(cudaMemsetAsync(c.b.phi, 0, vbytes, c.st));
     enqueue_init(c, true);
@@ -976,12 +1097,14 @@ rd_status rd_query(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npai
             rd_status one = RD_OK;
             RD_TRY(query_batch(g, s + p, t + p, 1, o, true, r_out + p, iters_out ? iters_out + p : nullptr,
                                err_est_out ? err_est_out + p : nullptr,
-                               pair_status_out ? pair_status_out + p : nullptr, st, &one, &ev));
+                               pair_status_out ? pair_status_out + p : nullptr, st, &one, &ev, false, true));
             if (one == RD_WARN_NOT_CONVERGED) call = one;
         }
         return call;
     }
-    RD_TRY(query_batch(g, s, t, npairs, o, false, r_out, iters_out, err_est_out, pair_status_out, st, &call, &ev));
+    const bool compact = (o.flags & RD_Q_NO_COMPACT) == 0;
+    RD_TRY(query_batch(g, s, t, npairs, o, false, r_out, iters_out, err_est_out, pair_status_out, st, &call, &ev,
+                       compact, true));
     return call;
 }
 

@@ -113,9 +113,30 @@ struct FinArgs {
     double rel_tol, resid_tol, sumdeg;
     const double* block_part;
     PairState st;
-    void* cf_hist;                      // T [k_max+1][4][ld]
+    int64_t pstride;                    // stride of the per-pair [k][pair] arrays (original ld)
+    const int32_t* slot_pair;           // column slot -> pair (-1: empty); NULL = identity
+    void* cf_step;                      // T [4][ld]: rows 1..3 receive alpha_i, c_i, 1/beta_{i+1}
+    void* cf_next;                      // T [4][ld]: row 0 receives beta_{i+1} for the next step
     int elem_size;
 };
+
+// Column compaction: keep the slots whose pair is still active, in slot order.
+struct CompactArgs {
+    int64_t n, ld_old, ld_new;
+    const int32_t* slot_pair_old;       // NULL = identity over npairs
+    int npairs;
+    int32_t* slot_pair_new;             // ld_new
+    int32_t* old_slot;                  // ld_new: source slot or -1
+    const int32_t* active;              // per pair
+    const void* cf_old;                 // T [4][ld_old]
+    void* cf_new;                       // T [4][ld_new]
+    const void* q_src0;                 // T n x ld_old
+    const void* q_src1;
+    void* q_dst0;                       // T n x ld_new
+    void* q_dst1;
+    int elem_size;
+};
+void launch_compact(cudaStream_t st, int grid, const CompactArgs& a);
 
 // --------------------------------------------------------------- graph
 struct Workspace {

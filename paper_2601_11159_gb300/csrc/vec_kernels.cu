@@ -99,9 +99,9 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
     part[1][split][lane] = s1;
     part[2][split][lane] = s2;
     __syncthreads();
-    if (split != 0 || col >= a.npairs) return;
-    const int p = (int)col;
-    if (!st.active[p]) return;
+    if (split != 0 || col >= a.ld) return;
+    const int p = a.slot_pair ? a.slot_pair[col] : (col < a.npairs ? (int)col : -1);
+    if (p < 0 || !st.active[p]) return;
     double A = 0.0, B = 0.0, C = 0.0;
 #pragma unroll
     for (int sp = 0; sp < 8; ++sp) {
@@ -111,7 +111,9 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
     }
     const int j = a.step;       // 0-based step index; Lanczos step i = j + 1
     const int64_t ld = a.ld;
-    T* cf = static_cast<T*>(a.cf_hist);
+    const int64_t np = a.pstride;  // stride of the per-pair arrays
+    T* cfs = static_cast<T*>(a.cf_step);
+    T* cfn = static_cast<T*>(a.cf_next);
     const double alpha = A;
     const double beta_i = st.beta[p];
     const double cdef = a.deflate ? C / a.sumdeg : 0.0;
@@ -126,52 +128,57 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
         delta = (1.0 - alpha) - beta_i * beta_i / dprev;
         g = st.g[p] * beta_i / dprev;
     }
-    const bool ok = isfinite(alpha) && isfinite(beta2) && isfinite(delta) && delta > 0.0;
-    if (!ok) {
-        st.status[p] = RD_ERR_NUMERIC;
-        st.active[p] = 0;
-        return;  // coefficients stay zero: the column is frozen at its last good estimate
-    }
-    const double incr = g * g / delta;
-    const double S = st.S[p] + incr;
-    st.S[p] = S;
-    st.r[p] = st.b2[p] * S;
-    st.ring[(int64_t)(j % kRing) * ld + p] = incr;
-    const double beta_next = sqrt(fmax(beta2, 0.0));
-    const double resid = beta_next * fabs(g / delta);
-    st.resid[p] = resid;
-    double tail = 0.0;
-    const int nr = j + 1 < kRing ? j + 1 : kRing;
-    for (int q = 0; q < nr; ++q) tail += st.ring[(int64_t)q * ld + p];
-    const double est = tail / S;
-    st.err[p] = est;
-    st.hist_alpha[(int64_t)j * ld + p] = alpha;
-    st.hist_beta[(int64_t)(j + 1) * ld + p] = beta_next;
-    st.k[p] = j + 1;
-    st.delta[p] = delta;
-    st.g[p] = g;
-
-    const double brk = a.fp64 ? 1e-12 : 1e-6;
     bool stop = false;
-    if (beta_next <= brk * (fabs(alpha) + beta_i)) {
-        stop = true;  // Krylov space exhausted: T_i is exact
-        st.err[p] = 0.0;
-    } else if (!a.fixed_k) {
-        if (a.resid_tol > 0.0 && resid <= a.resid_tol) stop = true;
-        if (a.rel_tol > 0.0 && j + 1 >= kRing && est <= a.rel_tol) stop = true;
-    }
-    if (!stop && j + 1 >= a.k_max) {
+    const bool ok = isfinite(alpha) && isfinite(beta2) && isfinite(delta) && delta > 0.0;
+    double beta_next = 0.0;
+    if (!ok) {
+        st.status[p] = RD_ERR_NUMERIC;  // frozen at its last good estimate
         stop = true;
-        if (!a.fixed_k) st.status[p] = RD_WARN_NOT_CONVERGED;
+    } else {
+        const double incr = g * g / delta;
+        const double S = st.S[p] + incr;
+        st.S[p] = S;
+        st.r[p] = st.b2[p] * S;
+        st.ring[(int64_t)(j % kRing) * np + p] = incr;
+        beta_next = sqrt(fmax(beta2, 0.0));
+        const double resid = beta_next * fabs(g / delta);
+        st.resid[p] = resid;
+        double tail = 0.0;
+        const int nr = j + 1 < kRing ? j + 1 : kRing;
+        for (int q = 0; q < nr; ++q) tail += st.ring[(int64_t)q * np + p];
+        const double est = tail / S;
+        st.err[p] = est;
+        st.hist_alpha[(int64_t)j * np + p] = alpha;
+        st.hist_beta[(int64_t)(j + 1) * np + p] = beta_next;
+        st.k[p] = j + 1;
+        st.delta[p] = delta;
+        st.g[p] = g;
+        const double brk = a.fp64 ? 1e-12 : 1e-6;
+        if (beta_next <= brk * (fabs(alpha) + beta_i)) {
+            stop = true;  // Krylov space exhausted: T_i is exact
+            st.err[p] = 0.0;
+        } else if (!a.fixed_k) {
+            if (a.resid_tol > 0.0 && resid <= a.resid_tol) stop = true;
+            if (a.rel_tol > 0.0 && j + 1 >= kRing && est <= a.rel_tol) stop = true;
+        }
+        if (!stop && j + 1 >= a.k_max) {
+            stop = true;
+            if (!a.fixed_k) st.status[p] = RD_WARN_NOT_CONVERGED;
+        }
     }
     if (stop) {
+        // zero coefficients: the column's vectors become (and stay) zero
         st.active[p] = 0;
-        return;  // zero coefficients from here on (the history was zeroed at start)
+        cfs[1 * ld + col] = T(0);
+        cfs[2 * ld + col] = T(0);
+        cfs[3 * ld + col] = T(0);
+        cfn[col] = T(0);
+        return;
     }
-    cf[((int64_t)j * 4 + 1) * ld + p] = (T)alpha;
-    cf[((int64_t)j * 4 + 2) * ld + p] = (T)cdef;
-    cf[((int64_t)j * 4 + 3) * ld + p] = (T)(1.0 / beta_next);
-    cf[((int64_t)(j + 1) * 4 + 0) * ld + p] = (T)beta_next;
+    cfs[1 * ld + col] = (T)alpha;
+    cfs[2 * ld + col] = (T)cdef;
+    cfs[3 * ld + col] = (T)(1.0 / beta_next);
+    cfn[col] = (T)beta_next;
     st.beta[p] = beta_next;
     atomicAdd(&st.act_count[j + 1], 1);
 }
@@ -382,5 +389,85 @@ static void launch_eg(int grid, cudaStream_t st, const EdgeGradArgs<T>& a)
 
 void launch_edge_grad_f32(int grid, cudaStream_t st, const EdgeGradArgs<float>& a) { launch_eg<float>(grid, st, a); }
 void launch_edge_grad_f64(int grid, cudaStream_t st, const EdgeGradArgs<double>& a) { launch_eg<double>(grid, st, a); }
+
+// --------------------------------------------------------------- compaction
+// Slot map of the still-active pairs, in slot order (one block, chunked block scan), and
+// the coefficients of the next step moved to the new slots.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_compact_map(const CompactArgs a)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int base_s;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) base_s = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < a.ld_old; c0 += blockDim.x) {
+        const int64_t slot = c0 + tid;
+        int p = -1;
+        if (slot < a.ld_old) p = a.slot_pair_old ? a.slot_pair_old[slot] : (slot < a.npairs ? (int)slot : -1);
+        const int keep = (p >= 0 && a.active[p]) ? 1 : 0;
+        // block-wide exclusive scan of keep
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int in_warp = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[w] = __popc(bal);
+        __syncthreads();
+        int before = 0;
+        for (int i = 0; i < w; ++i) before += warp_tot[i];
+        int chunk_total = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) chunk_total += warp_tot[i];
+        const int dst = base_s + before + in_warp;
+        if (keep && dst < a.ld_new) {
+            a.slot_pair_new[dst] = p;
+            a.old_slot[dst] = (int)slot;
+        }
+        __syncthreads();
+        if (tid == 0) base_s += chunk_total;
+        __syncthreads();
+    }
+    const int kept = base_s;
+    const T* cfo = static_cast<const T*>(a.cf_old);
+    T* cfn = static_cast<T*>(a.cf_new);
+    for (int64_t d = tid; d < a.ld_new; d += blockDim.x) {
+        if (d >= kept) {
+            a.slot_pair_new[d] = -1;
+            a.old_slot[d] = -1;
+        }
+    }
+    __syncthreads();
+    for (int64_t d = tid; d < a.ld_new; d += blockDim.x) {
+        const int o = a.old_slot[d];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfn[q * a.ld_new + d] = o >= 0 ? cfo[q * a.ld_old + o] : T(0);
+    }
+}
+
+// q blocks copied column-wise into the compact layout (empty slots zero).
+template <typename T>
+__global__ void __launch_bounds__(256) k_compact_cols(const CompactArgs a)
+{
+    const int64_t total = a.n * a.ld_new;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const T* s0 = static_cast<const T*>(a.q_src0);
+    const T* s1 = static_cast<const T*>(a.q_src1);
+    T* d0 = static_cast<T*>(a.q_dst0);
+    T* d1 = static_cast<T*>(a.q_dst1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int64_t u = i / a.ld_new, c = i % a.ld_new;
+        const int o = a.old_slot[c];
+        d0[i] = o >= 0 ? s0[u * a.ld_old + o] : T(0);
+        d1[i] = o >= 0 ? s1[u * a.ld_old + o] : T(0);
+    }
+}
+
+void launch_compact(cudaStream_t st, int grid, const CompactArgs& a)
+{
+    if (a.elem_size == 8) {
+        k_compact_map<double><<<1, 1024, 0, st>>>(a);
+        k_compact_cols<double><<<grid, 256, 0, st>>>(a);
+    } else {
+        k_compact_map<float><<<1, 1024, 0, st>>>(a);
+        k_compact_cols<float><<<grid, 256, 0, st>>>(a);
+    }
+}
 
 }  // namespace rd

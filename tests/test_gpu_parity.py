@@ -251,3 +251,29 @@ def test_torch_device_io_and_autograd(rd):
     refg = dense.DenseRD.of(g).edge_grad(s, t, np.arange(1, 6, dtype=np.float64))
     got = w.grad.cpu().numpy().astype(np.float64)
     assert np.abs(got - refg).max() / np.abs(refg).max() < 1e-6
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_compaction_matches_fixed_layout(rd, mode):
+    """Packing converged pairs into narrower blocks changes no pair's result beyond the
+    reduction-order rounding of the narrower kernels (which can move a borderline stop
+    decision by one step, so both runs are also compared with the oracle)."""
+    if mode == "fp64":
+        g = F.grid_deleted(60, 0.05, 11)     # distances vary, so pairs stop at different k
+        s, t = F.random_pairs(g.n, 200, 13)
+        kw = dict(mode=mode, k_max=600, rel_tol=1e-10)
+        ref = dense.DenseRD.of(g).r(s, t)
+        tol_ab, tol_ref = 1e-8, 1e-8
+    else:
+        g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 200, 31)
+        kw = dict(mode=mode, k_max=200, rel_tol=1e-7)
+        ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=200, stop_tol=1e-13, threads=0)
+        tol_ab, tol_ref = 2e-6, FP32_TOL
+    G = rd.Graph.from_csr(g)
+    a = G.query(s, t, **kw)
+    st = G.last_stats()
+    b = G.query(s, t, compact=False, **kw)
+    assert st["compactions"] >= 1
+    assert np.abs(a.iters.astype(int) - b.iters.astype(int)).max() <= 1
+    assert rel(a.r, b.r).max() < tol_ab
+    assert rel(a.r, ref).max() < tol_ref
