@@ -633,6 +633,8 @@ static rd_status enqueue_compaction(RunCtx& c, int active_upper)
     o2.rhs_tile = 0;
     RD_TRY(make_plan(c.g, active_upper, o2, false, &np));
     if (np.ld >= c.cur.ld) return RD_OK;
+    // the spare region holds n x ld0 elements: two packed blocks must fit in it
+    if (!c.in_region_x && 2 * np.ld > c.pl.ld) return RD_OK;
     const int64_t n = c.g->n;
     void* dst0;
     void* dst1;
