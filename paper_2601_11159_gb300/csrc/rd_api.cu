@@ -396,14 +396,22 @@ struct Buffers {
     size_t state_bytes_begin, state_bytes_end;  // offsets of the region zeroed per query
 };
 
+// Byte size of an n x ld block rounded up to 256 bytes, so that every block that follows
+// another inside a region starts 256-byte aligned (the kernels use 16-byte vector accesses).
+static int64_t block_bytes(int64_t n, int64_t ld, size_t elem)
+{
+    return ((n * ld * (int64_t)elem) + 255) & ~int64_t(255);
+}
+
 static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, bool grad, Buffers* b,
                     bool compact = false)
 {
     const int64_t ld = pl.ld, n = g->n, K = pl.k_max;
-    b->region_a = c.take<char>(2 * n * ld * pl.elem);
+    b->region_a = c.take<char>(2 * block_bytes(n, ld, pl.elem));
     b->q[0] = b->region_a;
-    b->q[1] = static_cast<char*>(b->region_a) + n * ld * pl.elem;
-    b->region_x = compact ? c.take<char>(n * ld * pl.elem) : nullptr;
+    b->q[1] = static_cast<char*>(b->region_a) + block_bytes(n, ld, pl.elem);
+    // spare region: two packed blocks of at most ld/2 columns, each rounded to 256 bytes
+    b->region_x = compact ? c.take<char>(block_bytes(n, ld, pl.elem) + 512) : nullptr;
     b->heavy_part = c.take<char>(std::max<int64_t>(g->n_chunks, 1) * ld * pl.elem);
     // sized for any column tile and any grid of up to 8 blocks of kBlock threads per SM
     b->block_part = c.take<double>((size_t)ld * 3 * (size_t)std::max(pl.grid_main, g->sm_count * 8));
@@ -643,7 +651,7 @@ static rd_status enqueue_compaction(RunCtx& c, int active_upper)
     } else {
         dst0 = c.b.region_x;
     }
-    dst1 = static_cast<char*>(dst0) + n * np.ld * (int64_t)np.elem;
+    dst1 = static_cast<char*>(dst0) + block_bytes(n, np.ld, np.elem);
     CompactArgs a{};
     a.n = n;
     a.ld_old = c.cur.ld;
