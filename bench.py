@@ -4,8 +4,8 @@
 Workload: Chung-Lu power-law graph (n = 1,000,000 before the largest-component cut,
 exponent 2.1, mean degree 20, 1e7 endpoint draws, unweighted) with 256 uniform random
 (s,t) pairs answered in one batched query; FP32 vectors, FP64 alpha/beta/T_k; each pair
-stops when its estimated relative error is below 1e-7 (target: true relative error
-<= 1e-6, checked against the FP64 oracle on a sample of pairs).
+stops when its estimated relative error is below 1e-6; the true relative error of every
+pair is then checked against the FP64 oracle (max_rel_err).
 
 One step = one full query of the 256 pairs (every Lanczos step of every pair).
 value = pairs/s over all ranks with the pair ids already on the device; e2e = the same
@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RD (s,t) pairs/sec at rel.err<=1e-6 (batched Lanczos, Chung-Lu 1M, 256 pairs)"
 UNIT = "pairs/s"
-REL_TOL = 1e-7
+REL_TOL = 1e-6
 K_MAX = 200
 
 
@@ -196,7 +196,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-sample", type=int, default=32)
-    ap.add_argument("--cpu-sample", type=int, default=32)
+    ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--plain-sample", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -335,7 +335,8 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
         rel = np.abs(r_gpu[:cs] - r_or) / np.abs(r_or)
         max_rel = float(rel.max())
         cpu = {"value": cs / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
-               "sample": f"{cs} of the 256 pairs, FP64 C Lanczos, stop at relative increment 1e-9",
+               "sample": f"{cs} of the {P} pairs, FP64 C Lanczos, stop at relative increment 1e-9; the same "
+                         f"run gives the reference values for max_rel_err",
                "max_rel_err_gpu_vs_oracle": max_rel, "median_rel_err_gpu_vs_oracle": float(np.median(rel))}
         if plain_r is not None:
             ps = plain_r.size

@@ -547,6 +547,8 @@ static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
     a.heavy_part = static_cast<T*>(c.b.heavy_part);
     a.ntasks = g->ntasks;
     a.task_row = g->task_row;
+    // rows whose current slab fits in half of L2 are gathered with L2 priority
+    a.hot_rows = g->l2_bytes > 0 ? (int64_t)(g->l2_bytes / 2) / (c.cur.cfg.tp() * (int64_t)sizeof(T)) : 0;
     a.block_part = c.b.block_part;
     a.active_prev = reduce ? c.b.st.act_count + j : nullptr;
     a.do_reduce = reduce ? 1 : 0;
@@ -1016,12 +1018,15 @@ rd_status rd_graph_create(rd_graph** out, int64_t n, int64_t nnz, const int64_t*
     rd_graph* g = new rd_graph();
     g->n = n;
     g->nnz_in = nnz;
+    int l2 = 0;
     if (cudaGetDevice(&g->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+        cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device) != cudaSuccess) {
         rd_status s = cuda_status(cudaGetLastError(), "cudaGetDevice");
         delete g;
         return s == RD_OK ? RD_ERR_CUDA : s;
     }
+    g->l2_bytes = l2;
     rd_status s = graph_build(g, row_ptr, col_idx, weights, flags, static_cast<cudaStream_t>(stream));
     if (s < 0) {
         free_graph(g);

@@ -69,6 +69,7 @@ struct StepArgs {
     const int32_t* chunk_beg;      // nnz range of each chunk
     const int32_t* chunk_end;
     T* heavy_part;                 // n_chunks x ld
+    int64_t hot_rows;              // gathers of rows below this id keep L2 priority (the rest evict first)
     int64_t ntasks;                // row-stream tasks: rows [task_row[i], task_row[i+1])
     const int32_t* task_row;
     double* block_part;            // [slab][block][3][TP]
@@ -176,6 +177,7 @@ struct rd_graph {
     rd::Workspace ws;
     rd_call_stats stats{};
     int* h_pinned = nullptr;          // small pinned host buffer for polls
+    int64_t l2_bytes = 0;             // device L2 size
 };
 
 namespace rd {

@@ -132,6 +132,53 @@ __device__ __forceinline__ void st_plain(T* p, const T (&r)[VEC])
     }
 }
 
+// Gathers with an L2 eviction-priority hint (createpolicy + ld.global.nc.L2::cache_hint):
+// rows that many nonzeros point to are kept (evict_last), the long tail of rarely
+// gathered rows is let go first (evict_first), so the tail does not push the hot rows
+// out of L2.
+#ifndef RD_GATHER_HINT
+#define RD_GATHER_HINT 1
+#endif
+
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ float4 ld_f4_policy(const float4* p, uint64_t pol)
+{
+    float4 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void ld_gather_pol(T (&r)[VEC], const T* p, uint64_t pol)
+{
+    constexpr int B = (int)sizeof(T) * VEC;
+    if constexpr (B >= 16) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int i = 0; i < B / 16; ++i) {
+            float4 x = ld_f4_policy(q + i, pol);
+            memcpy(&r[i * (16 / (int)sizeof(T))], &x, 16);
+        }
+    } else {
+        ld_gather<T, VEC>(r, p);
+    }
+}
+
 // ------------------------------------------------------------ accumulators
 // FP32 partial sums use Kahan compensation (error independent of the number of
 // terms to first order); FP64 sums are plain.
@@ -575,6 +622,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
     const int64_t ld = a.ld;
     const uint32_t ldv = (uint32_t)(ld / VEC);  // row stride in VEC-element units
     const int ntasks = (int)a.ntasks;
+#if RD_GATHER_HINT
+    const uint64_t pol_hot = l2_policy_evict_last(), pol_cold = l2_policy_evict_first();
+    const uint32_t hot_off = (uint32_t)(a.hot_rows < (int64_t)(0xffffffffu / (ldv ? ldv : 1)) ? a.hot_rows * ldv
+                                                                                              : 0xffffffffu);
+#endif
 
     for (int slab = 0; slab < nslab; ++slab) {
         const int64_t c0 = (int64_t)slab * TP + gl * VEC;
@@ -638,7 +690,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
                         const uint32_t off = __shfl_sync(mask, my_off[hh], kk % GS, GS);
                         if constexpr (WEIGHTED) wu[u] = (T)__shfl_sync(mask, my_w[hh], kk % GS, GS);
                         if (kk < cnt) {
+#if RD_GATHER_HINT
+                            ld_gather_pol<T, VEC>(x[u], q + (size_t)off * VEC, off < hot_off ? pol_hot : pol_cold);
+#else
                             ld_gather<T, VEC>(x[u], q + (size_t)off * VEC);
+#endif
                         } else {
 #pragma unroll
                             for (int i = 0; i < VEC; ++i) x[u][i] = T(0);
