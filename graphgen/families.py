@@ -15,7 +15,7 @@ from typing import Optional
 import numpy as np
 
 from . import rng
-from .graph import CSRGraph, largest_component, to_csr, unique_undirected
+from .graph import CSRGraph, largest_component, to_csr, unique_undirected  # noqa: F401
 
 # Stream ids (arbitrary constants, one per independent use of randomness).
 _S_CL_A, _S_CL_B = 11, 12
@@ -157,11 +157,24 @@ def chung_lu(n: int, gamma: float, mean_degree: float, m0: int, seed: int) -> CS
     return out
 
 
-def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int) -> CSRGraph:
+def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int, fast: bool = True) -> CSRGraph:
     """R-MAT (Chakrabarti, Zhan and Faloutsos, SDM 2004): each of edge_factor * 2^scale edges
     picks one of four quadrants per level with probabilities (a, b, c, 1-a-b-c). No noise and
-    no vertex permutation; symmetrised, deduplicated, largest component kept."""
+    no vertex permutation; symmetrised, deduplicated, largest component kept. ``fast`` uses the
+    C generator (same random streams, identical graph)."""
     n = 1 << scale
+    if fast:
+        from . import fast as FG
+
+        u, v = FG.rmat_edges(scale, edge_factor * n, a, b, c, seed, _S_RMAT)
+        row_ptr, col = FG.csr_from_edges(n, u, v)
+        del u, v
+        g = CSRGraph(n, row_ptr, col, None, f"rmat{scale}")
+        g.meta = {"scale": scale, "edge_factor": edge_factor, "abc": (a, b, c), "seed": seed}
+        out = largest_component(g)
+        out.meta = dict(out.meta or {})
+        out.meta.update(g.meta)
+        return out
     m = edge_factor * n
     chunk = 1 << 22
     ab, abc = a + b, a + b + c

@@ -92,18 +92,25 @@ def component_labels(g: CSRGraph) -> np.ndarray:
 
 
 def largest_component(g: CSRGraph) -> CSRGraph:
-    """Induced subgraph on the largest connected component, vertex order preserved."""
+    """Induced subgraph on the largest connected component, vertex order preserved.
+
+    A component is closed under adjacency, so the kept rows keep all their entries; the
+    relabelling is monotone, so rows and columns stay sorted without re-sorting."""
     labels = component_labels(g)
     counts = np.bincount(labels)
     big = int(np.argmax(counts))
     keep = labels == big
     if keep.all():
         return g
-    new_id = np.full(g.n, -1, dtype=np.int64)
-    new_id[keep] = np.arange(int(keep.sum()), dtype=np.int64)
-    a, b, w = g.undirected_edges()
-    sel = keep[a] & keep[b]
-    out = to_csr(int(keep.sum()), new_id[a[sel]], new_id[b[sel]], None if w is None else w[sel], g.name)
+    new_id = np.cumsum(keep, dtype=np.int64) - 1
+    deg = np.diff(g.row_ptr)
+    entry_keep = np.repeat(keep, deg)
+    n2 = int(keep.sum())
+    row_ptr = np.zeros(n2 + 1, dtype=np.int64)
+    np.cumsum(deg[keep], out=row_ptr[1:])
+    col = new_id[g.col[entry_keep]].astype(np.int32)
+    w = None if g.w is None else g.w[entry_keep]
+    out = CSRGraph(n2, row_ptr, col, w, g.name)
     out.meta = dict(g.meta or {})
     out.meta["lcc_dropped_vertices"] = int(g.n - out.n)
     out.meta["lcc_old_id"] = np.nonzero(keep)[0]
