@@ -113,14 +113,18 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
+def dist_setup(backend: str = None):
+    """One process per GPU (torchrun env). Ranks share nothing on the data path: each answers
+    its own pairs; the process group only carries the barrier and the max of the timings."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
 
-        backend = "nccl"
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
     return world, rank, local
 
@@ -133,20 +137,38 @@ def barrier(world):
 
 
 def allmax(world, x: float) -> float:
+    """Max over ranks of a host scalar (the slowest rank sets the job's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of rank r's pair set (weak scaling: every rank answers its own 256 pairs)."""
+    from graphgen import workloads as W
+
+    return W.BASE_SEED + 2 + 1000 * rank
+
+
+def job_throughput(pairs_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job pairs/s: all ranks' pairs over the slowest rank's time."""
+    return pairs_per_rank * world * steps / (ms_max / 1000.0)
 
 
 def workload(rank: int, n: int = 1_000_000, pairs: int = 256):
     from graphgen import workloads as W
 
-    g, s, t = W.chunglu(n, 2.1, 20.0, n * 10, pairs, W.BASE_SEED + 2 + 1000 * rank)
+    # the graph is the same on every rank (the seed of rank 0); the pairs are the rank's own
+    g, _, _ = W.chunglu(n, 2.1, 20.0, n * 10, pairs, rank_seed(0))
+    from graphgen import families as F
+
+    s, t = F.random_pairs(g.n, pairs, rank_seed(rank))
     return g, s, t
 
 
@@ -261,7 +283,7 @@ def main():
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     ms_max = allmax(world, ms)
-    value = P * world * args.steps / (ms_max / 1000.0)
+    value = job_throughput(P, world, args.steps, ms_max)
     r_gpu = res.r.cpu().numpy()
     iters = res.iters.cpu().numpy()
     status = res.status.cpu().numpy()

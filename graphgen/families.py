@@ -208,10 +208,16 @@ def erdos_renyi(n: int, m: int, seed: int) -> CSRGraph:
     return largest_component(g)
 
 
-def barabasi_albert(n: int, m_attach: int, seed: int) -> CSRGraph:
+def barabasi_albert(n: int, m_attach: int, seed: int, fast: bool = True) -> CSRGraph:
     """Preferential attachment: each new vertex links to ``m_attach`` endpoints drawn from the
-    list of all earlier edge endpoints (plus a seed clique); duplicates dropped."""
+    list of all earlier edge endpoints (plus a seed clique); duplicates dropped. ``fast`` uses
+    the C generator (same draws, identical graph)."""
     m0 = m_attach + 1
+    if fast:
+        from . import fast as FG
+
+        src, dst = FG.ba_edges(n, m_attach, seed, _S_BA)
+        return to_csr(n, *unique_undirected(src, dst), name=f"ba{n}")
     a0, b0 = np.triu_indices(m0, 1)
     ends = list(np.concatenate([a0, b0]))
     src, dst = list(a0), list(b0)

@@ -36,6 +36,8 @@ def load():
             lib.gg_rmat_edges.restype = None
             lib.gg_csr_from_edges.argtypes = [C.c_int64, C.c_int64, P, P, P, P]
             lib.gg_csr_from_edges.restype = C.c_int64
+            lib.gg_ba_edges.argtypes = [C.c_int64, C.c_int, C.c_uint64, C.c_uint64, P, P]
+            lib.gg_ba_edges.restype = C.c_int64
             _lib = lib
         return _lib
 
@@ -57,3 +59,13 @@ def csr_from_edges(n: int, u: np.ndarray, v: np.ndarray):
     col = np.empty(2 * u.size, dtype=np.int32)
     nnz = lib.gg_csr_from_edges(n, u.size, u.ctypes.data, v.ctypes.data, row_ptr.ctypes.data, col.ctypes.data)
     return row_ptr, col[:nnz].copy()
+
+
+def ba_edges(n: int, m_attach: int, seed: int, stream: int):
+    lib = load()
+    m0 = m_attach + 1
+    cap = m0 * (m0 - 1) // 2 + (n - m0) * m_attach + 16
+    src = np.empty(cap, dtype=np.int64)
+    dst = np.empty(cap, dtype=np.int64)
+    k = lib.gg_ba_edges(n, m_attach, seed & 0xFFFFFFFFFFFFFFFF, stream, src.ctypes.data, dst.ctypes.data)
+    return src[:k], dst[:k]

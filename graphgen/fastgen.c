@@ -113,3 +113,43 @@ int64_t gg_csr_from_edges(int64_t n, int64_t m, const int64_t *u, const int64_t 
     free(fill);
     return nnz;
 }
+
+/* Barabasi-Albert preferential attachment with the same draws as graphgen.families:
+ * a clique on m_attach+1 seed vertices; vertex v >= m_attach+1 picks m_attach targets, each
+ * the endpoint at position floor(u * L) of the current endpoint list (L its length), where u
+ * is draw k of the stream; after its m_attach picks, the targets and then v (m_attach times)
+ * are appended to the list. Writes the directed pick list (src, dst) including the clique;
+ * returns the number of pairs (duplicates are removed later). */
+int64_t gg_ba_edges(int64_t n, int m_attach, uint64_t seed, uint64_t stream, int64_t *src, int64_t *dst)
+{
+    const uint64_t key = gg_stream_key(seed, stream);
+    const int64_t m0 = m_attach + 1;
+    const int64_t cap_ends = m0 * (m0 - 1) + 2 * (n - m0) * (int64_t)m_attach + 16;
+    int64_t *ends = malloc(sizeof(int64_t) * (size_t)cap_ends);
+    int64_t L = 0, np = 0;
+    /* clique edges in numpy's triu order, ends = all a's then all b's */
+    for (int64_t i = 0; i < m0; ++i)
+        for (int64_t j = i + 1; j < m0; ++j) {
+            src[np] = i;
+            dst[np] = j;
+            ++np;
+        }
+    for (int64_t k = 0; k < np; ++k) ends[L++] = src[k];
+    for (int64_t k = 0; k < np; ++k) ends[L++] = dst[k];
+    uint64_t draw = 0;
+    for (int64_t v = m0; v < n; ++v) {
+        const int64_t Lv = L;
+        const int64_t first = np;
+        for (int q = 0; q < m_attach; ++q) {
+            const double u = uniform_at(key, draw++);
+            const int64_t tgt = ends[(int64_t)(u * (double)Lv)];
+            src[np] = v;
+            dst[np] = tgt;
+            ++np;
+        }
+        for (int q = 0; q < m_attach; ++q) ends[L++] = dst[first + q];
+        for (int q = 0; q < m_attach; ++q) ends[L++] = v;
+    }
+    free(ends);
+    return np;
+}

@@ -184,6 +184,33 @@ rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t 
 rd_status rd_potential(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
                        const rd_query_opts* opts, float* phi_out, double* r_out, void* stream);
 
+/* Triangle-count edge weights for the weighted experiments (Section 6, Exp-2): for every stored
+ * entry e = (u, v), w_out[e] = number of triangles containing edge uv, or 1 if there is none.
+ * The graph's own weights are ignored; its rows must have strictly increasing columns
+ * (RD_ERR_INVALID_ARG otherwise). w_out: float[nnz], host or device. Pass the result to
+ * rd_graph_set_weights to run the weighted method. */
+rd_status rd_triangle_weights(const rd_graph* g, float* w_out, void* stream);
+
+/* Power Method (Section 2.2, Algorithm 1), batched over pairs on the same SpMM kernels: the
+ * truncated lazy-walk series rbar_l = 1/2 sum_{i=0..l} (e_s-e_t)^T D^{-1} (I/2 + P/2)^i (e_s-e_t),
+ * P = A D^{-1} (Eq. (er_laylor_expansion) truncated at l). A baseline for the Lanczos path.
+ *  steps     : l >= 0 (l + 1 terms).
+ *  mode      : rd_mode (vector precision; the sums are FP64).
+ *  r_out     : double[npairs], host or device.
+ *  r_hist_out: double[steps + 1][npairs] or NULL: the estimate after each term.
+ * Errors as rd_query (no per-pair status; disconnected pairs are not detected). */
+rd_status rd_power_method(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs, int32_t steps,
+                          int32_t mode, double* r_out, double* r_hist_out, void* stream);
+
+/* Electric flows (Section 6.3, Definition electric_flow): for every stored entry e = (u -> v),
+ * flow_out[p][e] = phi_p(u) - phi_p(v), with phi_p the Lanczos potential of pair p as in
+ * rd_potential (Algorithm 5, second line). The current through the edge is w_e * flow.
+ *  flow_out : float[npairs][nnz] (nnz as passed to create, caller's entry order; entries that
+ *             were self-loops get 0), host or device.
+ *  r_out    : double[npairs] or NULL. Errors as rd_query. */
+rd_status rd_flow(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
+                  const rd_query_opts* opts, float* flow_out, double* r_out, void* stream);
+
 /* Batched query without any device allocation -- no counterpart in the paper; it exists
  * for callers that cannot call cudaMalloc (code running under another framework's
  * allocator or memory pool, processes that reserve all device memory up front, or

@@ -29,7 +29,7 @@ from ._lib import (  # noqa: F401
 
 __all__ = ["Graph", "RDError", "query", "edge_grad", "potential", "graph_create", "graph_destroy",
            "graph_set_weights", "last_call_stats", "status_string", "ResistanceDistance", "lib",
-           "query_noalloc"]
+           "query_noalloc", "flow", "power_method"]
 
 
 def lib():
@@ -217,6 +217,34 @@ def potential(handle: int, n: int, s, t, stream=None, **kw):
     return phi.reshape(P, n), r
 
 
+def flow(handle: int, nnz_in: int, s, t, stream=None, **kw):
+    """rd_flow: returns (f[P, nnz] float32 potential differences per stored entry, r[P])."""
+    dev = _is_torch(s) and s.is_cuda
+    sp, ks = _arr(s, np.int32)
+    tp_, kt = _arr(t, np.int32)
+    P = ks.numel() if _is_torch(ks) else ks.size
+    f, fp = _out(dev, P * nnz_in, np.float32)
+    r, rp = _out(dev, P, np.float64)
+    o = _opts(**kw)
+    st = lib().rd_flow(handle, sp, tp_, P, C.byref(o), fp, rp, _stream_ptr(stream))
+    _check(st, "rd_flow")
+    return f.reshape(P, nnz_in), r
+
+
+def power_method(handle: int, s, t, steps: int, mode: str = "fp64", history: bool = False, stream=None):
+    """rd_power_method (Algorithm 1): returns (rbar[P], hist[steps+1, P] or None)."""
+    dev = _is_torch(s) and s.is_cuda
+    sp, ks = _arr(s, np.int32)
+    tp_, kt = _arr(t, np.int32)
+    P = ks.numel() if _is_torch(ks) else ks.size
+    r, rp = _out(dev, P, np.float64)
+    hist, hp = _out(dev, P * (steps + 1), np.float64) if history else (None, None)
+    m = RD_MODE_FP64 if mode in ("fp64", RD_MODE_FP64) else RD_MODE_FP32V_FP64S
+    st = lib().rd_power_method(handle, sp, tp_, P, int(steps), m, rp, hp, _stream_ptr(stream))
+    _check(st, "rd_power_method", ok=(RD_OK,))
+    return r, (None if hist is None else hist.reshape(steps + 1, P))
+
+
 def query_noalloc(row_ptr, col, w, s, t, stream=None, **kw):
     """rd_query_noalloc for callers that cannot allocate device memory: every array must be a
     CUDA tensor (the graph is used in place, no handle is created). Returns (r, iters) as CUDA
@@ -274,6 +302,18 @@ class Graph:
 
     def potential(self, s, t, **kw):
         return potential(self.handle, self.n, s, t, **kw)
+
+    def flow(self, s, t, **kw):
+        return flow(self.handle, self.nnz_in, s, t, **kw)
+
+    def triangle_weights(self, device: bool = False):
+        """rd_triangle_weights: float32[nnz] triangle counts per stored entry (1 where none)."""
+        w, wp = _out(device, self.nnz, np.float32)
+        _check(lib().rd_triangle_weights(self.handle, wp, _stream_ptr(None)), "rd_triangle_weights", ok=(RD_OK,))
+        return w
+
+    def power_method(self, s, t, steps: int, **kw):
+        return power_method(self.handle, s, t, steps, **kw)
 
     def last_stats(self) -> dict:
         return last_call_stats(self.handle)

@@ -75,6 +75,9 @@ EXPORTS = [
     "rd_query",
     "rd_edge_grad",
     "rd_potential",
+    "rd_flow",
+    "rd_power_method",
+    "rd_triangle_weights",
     "rd_query_noalloc",
     "rd_last_call_stats",
     "rd_status_string",
@@ -102,6 +105,12 @@ def declare(lib):
     lib.rd_edge_grad.restype = C.c_int
     lib.rd_potential.argtypes = [P, P, P, C.c_int64, C.POINTER(QueryOpts), P, P, P]
     lib.rd_potential.restype = C.c_int
+    lib.rd_flow.argtypes = [P, P, P, C.c_int64, C.POINTER(QueryOpts), P, P, P]
+    lib.rd_flow.restype = C.c_int
+    lib.rd_power_method.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P]
+    lib.rd_power_method.restype = C.c_int
+    lib.rd_triangle_weights.argtypes = [P, P, P]
+    lib.rd_triangle_weights.restype = C.c_int
     lib.rd_query_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, P, P, C.c_int64, C.POINTER(QueryOpts), P, P, P]
     lib.rd_query_noalloc.restype = C.c_int
     lib.rd_last_call_stats.argtypes = [P, C.POINTER(CallStats)]

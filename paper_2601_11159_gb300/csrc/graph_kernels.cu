@@ -207,3 +207,54 @@ rd_status compute_degrees_scratch(rd_graph* g, cudaStream_t st, void* flags_dev,
 }
 
 }  // namespace rd
+
+namespace rd {
+
+// Triangle-count weights (the weighted setting of the paper's Exp-2): for stored entry
+// e = (u, v), w(e) = |N(u) & N(v)| (the triangles through edge uv), or 1 when that is 0.
+// One thread per entry: every element of the shorter adjacency list is looked up in the
+// longer one by binary search (rows must be sorted by column).
+__global__ void k_triangle_weights(int64_t n, const int64_t* rp, const int32_t* col, float* w_out, int32_t* unsorted)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const int64_t a0 = rp[u], a1 = rp[u + 1];
+        for (int64_t e = a0; e < a1; ++e) {
+            if (e > a0 && col[e] <= col[e - 1]) atomicOr(unsorted, 1);
+            const int64_t v = col[e];
+            const int64_t b0 = rp[v], b1 = rp[v + 1];
+            int64_t s0 = a0, s1 = a1, l0 = b0, l1 = b1;  // shorter list [s0,s1), longer [l0,l1)
+            if (a1 - a0 > b1 - b0) {
+                s0 = b0; s1 = b1; l0 = a0; l1 = a1;
+            }
+            int64_t cnt = 0;
+            for (int64_t i = s0; i < s1; ++i) {
+                const int32_t x = col[i];
+                int64_t lo = l0, hi = l1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (col[mid] < x) lo = mid + 1; else hi = mid;
+                }
+                cnt += (lo < l1 && col[lo] == x);
+            }
+            w_out[e] = cnt > 0 ? (float)cnt : 1.0f;
+        }
+    }
+}
+
+rd_status triangle_weights(int64_t n, const int64_t* rp, const int32_t* col, float* w_out, int sm_count,
+                           cudaStream_t st, int32_t* flag_dev)
+{
+    RD_CUDA(cudaMemsetAsync(flag_dev, 0, sizeof(int32_t), st));
+    k_triangle_weights<<<grid_for(n, sm_count), 256, 0, st>>>(n, rp, col, w_out, flag_dev);
+    int32_t h = 0;
+    RD_CUDA(cudaMemcpyAsync(&h, flag_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("triangle weights need every row's columns sorted increasingly and without duplicates");
+        return RD_ERR_INVALID_ARG;
+    }
+    return RD_OK;
+}
+
+}  // namespace rd

@@ -498,6 +498,7 @@ struct RunCtx {
     bool lagged_polls = false;
     int cf_sel = 0, slot_sel = -1;  // slot_sel < 0: identity slot map
     bool in_region_x = false;
+    bool lazy_walk = false;  // Power Method steps instead of Lanczos steps
     int compactions = 0;
     EventPool* ev = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
@@ -552,6 +553,7 @@ static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
     a.block_part = c.b.block_part;
     a.active_prev = reduce ? c.b.st.act_count + j : nullptr;
     a.do_reduce = reduce ? 1 : 0;
+    a.lazy_walk = c.lazy_walk ? 1 : 0;
     return a;
 }
 
@@ -1246,6 +1248,191 @@ extern "C" rd_status rd_potential(rd_graph* g, const int32_t* s, const int32_t* 
     RD_TRY(finish_outputs(c, r_out, nullptr, nullptr, nullptr, &outs));
     record_stats(c);
     return outs;
+}
+
+namespace rd {
+// Potential differences along every stored entry (Section 6.3, Definition electric_flow:
+// f(e) = phi(u) - phi(v) for e = (u, v)); one warp per row, lanes over the row's entries,
+// output pair-major in the caller's entry order (dropped self-loops get 0).
+template <typename T>
+__global__ void k_flow(int64_t n, int64_t ld, int npairs, int64_t nnz_in, const int64_t* row_ptr,
+                       const int32_t* col, const int64_t* keep_idx, const T* phi, float* out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        for (int64_t e = row_ptr[u] + lane; e < row_ptr[u + 1]; e += 32) {
+            const int64_t v = col[e];
+            const int64_t oe = keep_idx ? keep_idx[e] : e;
+            for (int p = 0; p < npairs; ++p)
+                out[(int64_t)p * nnz_in + oe] = (float)(phi[u * ld + p] - phi[v * ld + p]);
+        }
+    }
+}
+}  // namespace rd
+
+extern "C" rd_status rd_flow(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs,
+                             const rd_query_opts* opts, float* flow_out, double* r_out, void* stream)
+{
+    g_last_error.clear();
+    rd_query_opts o;
+    RD_TRY(validate_common(g, s, t, npairs, opts, &o));
+    if (npairs > 0 && g->nnz_in > 0 && !flow_out) {
+        set_error("flow_out must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    g->stats = rd_call_stats{};
+    if (npairs == 0) return RD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EventPool ev;
+    RunCtx c;
+    c.ev = &ev;
+    RD_TRY(prepare_run(c, g, npairs, o, false, true, st));
+    rd_status call = RD_OK;
+    RD_TRY(forward_and_potential(c, s, t, nullptr, &call));
+    const size_t bytes = sizeof(float) * (size_t)g->nnz_in * (size_t)npairs;
+    const bool dev_out = is_device_ptr(flow_out);
+    float* stage = dev_out ? flow_out : nullptr;
+    if (!dev_out && bytes) RD_CUDA(cudaMallocAsync((void**)&stage, bytes, st));
+    if (g->keep_idx && bytes) RD_CUDA(cudaMemsetAsync(stage, 0, bytes, st));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g->sm_count * 8, (g->n + 7) / 8));
+    if (c.pl.fp64)
+        k_flow<double><<<grid, 256, 0, st>>>(g->n, c.pl.ld, (int)npairs, g->nnz_in, g->row_ptr, g->col, g->keep_idx,
+                                             static_cast<const double*>(c.b.phi), stage);
+    else
+        k_flow<float><<<grid, 256, 0, st>>>(g->n, c.pl.ld, (int)npairs, g->nnz_in, g->row_ptr, g->col, g->keep_idx,
+                                            static_cast<const float*>(c.b.phi), stage);
+    ++c.launches;
+    if (!dev_out && bytes) {
+        RD_CUDA(cudaMemcpyAsync(flow_out, stage, bytes, cudaMemcpyDeviceToHost, st));
+        RD_CUDA(cudaFreeAsync(stage, st));
+    }
+    rd_status outs = RD_OK;
+    RD_TRY(finish_outputs(c, r_out, nullptr, nullptr, nullptr, &outs));
+    record_stats(c);
+    return outs;
+}
+
+// ============================================================ Power Method
+// Algorithm 1 (Section 2.2) batched over pairs on the same SpMM kernels: in y = D^{-1} r
+// the lazy walk r <- (I/2 + P/2) r reads y <- y/2 + D^{-1} W y / 2, and the estimate gains
+// r(s)/(2 d_s) - r(t)/(2 d_t) = (y_s - y_t)/2 per step. A comparison baseline for the
+// Lanczos iteration, which needs far fewer steps on graphs with large condition number.
+namespace rd {
+template <typename T>
+static rd_status run_power_method(RunCtx& c, int steps, double* d_hist)
+{
+    const int64_t ld = c.pl.ld, n = c.g->n;
+    RD_CUDA(cudaMemsetAsync(c.b.q[0], 0, n * ld * sizeof(T), c.st));
+    RD_CUDA(cudaMemsetAsync(c.b.q[1], 0, n * ld * sizeof(T), c.st));
+    char* base = static_cast<char*>(c.g->ws.base);
+    RD_CUDA(cudaMemsetAsync(base + c.b.state_bytes_begin, 0, c.b.state_bytes_end - c.b.state_bytes_begin, c.st));
+    PmArgs pa{};
+    pa.n = n;
+    pa.ld = ld;
+    pa.npairs = (int)c.P;
+    pa.s = c.b.s;
+    pa.t = c.b.t;
+    pa.deg64 = c.g->deg64;
+    pa.rbar = c.b.st.r;
+    pa.hist = d_hist;
+    pa.elem_size = (int)sizeof(T);
+    pa.err_flag = c.b.err_flag;
+    pa.y = c.b.q[1];
+    launch_pm_init(c.st, pa);
+    ++c.launches;
+    int* h = c.g->h_pinned;
+    RD_CUDA(cudaMemcpyAsync(h, c.b.err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+    RD_CUDA(cudaStreamSynchronize(c.st));
+    if (h[0]) {
+        set_error("a pair id is outside [0, n)");
+        return RD_ERR_INVALID_ARG;
+    }
+    c.lazy_walk = true;
+    for (int i = 0; i <= steps; ++i) {
+        pa.y = c.b.q[1];
+        pa.step = i;
+        launch_pm_accum(c.st, pa);
+        ++c.launches;
+        if (i == steps) break;
+        RD_TRY(enqueue_spmm<T>(c, 0, false));  // writes y_{i+1} into q[0]
+        std::swap(c.b.q[0], c.b.q[1]);
+        c.steps = i + 1;
+    }
+    RD_CUDA(cudaGetLastError());
+    return RD_OK;
+}
+}  // namespace rd
+
+extern "C" rd_status rd_power_method(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs, int32_t steps,
+                                     int32_t mode, double* r_out, double* r_hist_out, void* stream)
+{
+    g_last_error.clear();
+    rd_query_opts o;
+    rd_query_opts_init(&o);
+    o.mode = mode;
+    o.k_max = steps + 1;
+    o.kernel = 1;  // row-group kernel (the heavy-row pre-pass and chunk sums apply as in rd_query)
+    if (steps < 0 || steps >= (1 << 22)) {
+        set_error("steps must be in [0, 2^22)");
+        return RD_ERR_INVALID_ARG;
+    }
+    RD_TRY(validate_common(g, s, t, npairs, &o, &o));
+    if (npairs > 0 && !r_out) {
+        set_error("r_out must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    g->stats = rd_call_stats{};
+    if (npairs == 0) return RD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EventPool ev;
+    RunCtx c;
+    c.ev = &ev;
+    RD_TRY(prepare_run(c, g, npairs, o, false, false, st));
+    RD_TRY(stage_pairs(c, s, t));
+    // the history reuses the alpha history block: (k_max) x ld doubles >= (steps + 1) x npairs
+    double* d_hist = c.b.st.hist_alpha;
+    rd_status rs = c.pl.fp64 ? run_power_method<double>(c, steps, d_hist) : run_power_method<float>(c, steps, d_hist);
+    if (rs < 0) return rs;
+    RD_CUDA(cudaMemcpyAsync(r_out, c.b.st.r, sizeof(double) * npairs, cudaMemcpyDefault, st));
+    if (r_hist_out)
+        RD_CUDA(cudaMemcpyAsync(r_hist_out, d_hist, sizeof(double) * npairs * (size_t)(steps + 1), cudaMemcpyDefault,
+                                st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    record_stats(c);
+    return RD_OK;
+}
+
+namespace rd {
+rd_status triangle_weights(int64_t n, const int64_t* rp, const int32_t* col, float* w_out, int sm_count,
+                           cudaStream_t st, int32_t* flag_dev);
+}
+
+extern "C" rd_status rd_triangle_weights(const rd_graph* g, float* w_out, void* stream)
+{
+    g_last_error.clear();
+    if (!g || (!w_out && g->nnz_in > 0)) {
+        set_error("graph and w_out must not be NULL");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (g->keep_idx) {
+        set_error("the graph had self-loops; pass a loop-free CSR for triangle weights");
+        return RD_ERR_UNSUPPORTED;
+    }
+    if (g->nnz == 0) return RD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool dev_out = is_device_ptr(w_out);
+    float* stage = dev_out ? w_out : nullptr;
+    int32_t* flag = nullptr;
+    RD_CUDA(cudaMallocAsync((void**)&flag, sizeof(int32_t), st));
+    if (!dev_out) RD_CUDA(cudaMallocAsync((void**)&stage, sizeof(float) * g->nnz, st));
+    rd_status rs = triangle_weights(g->n, g->row_ptr, g->col, stage, g->sm_count, st, flag);
+    if (rs == RD_OK && !dev_out)
+        RD_CUDA(cudaMemcpyAsync(w_out, stage, sizeof(float) * g->nnz, cudaMemcpyDeviceToHost, st));
+    if (!dev_out) cudaFreeAsync(stage, st);
+    cudaFreeAsync(flag, st);
+    RD_CUDA(cudaStreamSynchronize(st));
+    return rs;
 }
 
 // ===================================================== query without allocation

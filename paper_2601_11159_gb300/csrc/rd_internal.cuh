@@ -75,6 +75,7 @@ struct StepArgs {
     double* block_part;            // [slab][block][3][TP]
     const int32_t* active_prev;    // early exit when *active_prev == 0 (nullable)
     int do_reduce;
+    int lazy_walk;                 // Power Method step: W = (1/2) q + (1/2) D^{-1} W_adj q (no recurrence)
 };
 
 template <typename T>
@@ -138,6 +139,23 @@ struct CompactArgs {
     int elem_size;
 };
 void launch_compact(cudaStream_t st, int grid, const CompactArgs& a);
+
+// Power Method (Algorithm 1) in y = D^{-1} r: start y = D^{-1}(e_s - e_t), accumulate
+// rbar += (y_s - y_t)/2 per step (r(s)/(2 d_s) - r(t)/(2 d_t) of Algorithm 1).
+struct PmArgs {
+    int64_t n, ld;
+    int npairs;
+    const int32_t* s;
+    const int32_t* t;
+    const double* deg64;
+    void* y;                      // T n x ld
+    double* rbar;                 // npairs
+    double* hist;                 // nullable: [step][npairs]
+    int step, elem_size;
+    int32_t* err_flag;
+};
+void launch_pm_init(cudaStream_t st, const PmArgs& a);
+void launch_pm_accum(cudaStream_t st, const PmArgs& a);
 
 // --------------------------------------------------------------- graph
 struct Workspace {

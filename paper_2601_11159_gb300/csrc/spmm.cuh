@@ -318,8 +318,13 @@ __device__ __forceinline__ void row_epilogue(const StepArgs<T>& a, int64_t row, 
                                              Acc<T> (&sC)[VEC])
 {
     T wv[VEC];
+    if (a.lazy_walk) {
 #pragma unroll
-    for (int i = 0; i < VEC; ++i) wv[i] = invd * acc[i] - bt[i] * qp[i];
+        for (int i = 0; i < VEC; ++i) wv[i] = T(0.5) * (invd * acc[i]) + T(0.5) * qc[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) wv[i] = invd * acc[i] - bt[i] * qp[i];
+    }
     st_stream<T, VEC>(a.qprev_w + row * a.ld + c0, wv);
     if (a.do_reduce) {
 #pragma unroll
@@ -574,8 +579,13 @@ __device__ __forceinline__ void row_epilogue_b(const StepArgs<T>& a, int row, in
                                                const T (&qc)[VEC], RowBatch<T, VEC>& rb, SmemAcc<T, VEC>& sacc)
 {
     T wv[VEC];
+    if (a.lazy_walk) {
 #pragma unroll
-    for (int i = 0; i < VEC; ++i) wv[i] = invd * acc[i] - bt[i] * qp[i];
+        for (int i = 0; i < VEC; ++i) wv[i] = T(0.5) * (invd * acc[i]) + T(0.5) * qc[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) wv[i] = invd * acc[i] - bt[i] * qp[i];
+    }
     st_stream<T, VEC>(a.qprev_w + (int64_t)row * a.ld + c0, wv);
     if (a.do_reduce) {
 #pragma unroll

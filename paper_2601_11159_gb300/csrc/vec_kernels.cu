@@ -470,4 +470,52 @@ void launch_compact(cudaStream_t st, int grid, const CompactArgs& a)
     }
 }
 
+// ---------------------------------------------------------- Power Method
+template <typename T>
+__global__ void k_pm_init(const PmArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs) return;
+    const int32_t s = a.s[p], t = a.t[p];
+    if (s < 0 || (int64_t)s >= a.n || t < 0 || (int64_t)t >= a.n) {
+        atomicOr(a.err_flag, 1);
+        return;
+    }
+    a.rbar[p] = 0.0;
+    if (s == t) return;
+    T* y = static_cast<T*>(a.y);
+    y[(int64_t)s * a.ld + p] = (T)(1.0 / a.deg64[s]);
+    y[(int64_t)t * a.ld + p] = (T)(-1.0 / a.deg64[t]);
+}
+
+template <typename T>
+__global__ void k_pm_accum(const PmArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs) return;
+    const int32_t s = a.s[p], t = a.t[p];
+    if (s == t) {
+        if (a.hist) a.hist[(int64_t)a.step * a.npairs + p] = 0.0;
+        return;
+    }
+    const T* y = static_cast<const T*>(a.y);
+    const double r = a.rbar[p] + 0.5 * ((double)y[(int64_t)s * a.ld + p] - (double)y[(int64_t)t * a.ld + p]);
+    a.rbar[p] = r;
+    if (a.hist) a.hist[(int64_t)a.step * a.npairs + p] = r;
+}
+
+void launch_pm_init(cudaStream_t st, const PmArgs& a)
+{
+    const int nb = (a.npairs + 127) / 128;
+    if (a.elem_size == 8) k_pm_init<double><<<nb, 128, 0, st>>>(a);
+    else k_pm_init<float><<<nb, 128, 0, st>>>(a);
+}
+
+void launch_pm_accum(cudaStream_t st, const PmArgs& a)
+{
+    const int nb = (a.npairs + 127) / 128;
+    if (a.elem_size == 8) k_pm_accum<double><<<nb, 128, 0, st>>>(a);
+    else k_pm_accum<float><<<nb, 128, 0, st>>>(a);
+}
+
 }  // namespace rd

@@ -10,7 +10,7 @@ import pytest
 from graphgen import families as F
 from graphgen import workloads as W
 from graphgen.graph import to_csr
-from oracle import dense, lanczos
+from oracle import dense, lanczos, power
 from tests import closed_forms as CF
 
 pytestmark = pytest.mark.gpu
@@ -277,3 +277,72 @@ def test_compaction_matches_fixed_layout(rd, mode):
     assert np.abs(a.iters.astype(int) - b.iters.astype(int)).max() <= 1
     assert rel(a.r, b.r).max() < tol_ab
     assert rel(a.r, ref).max() < tol_ref
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_flow_kirchhoff_and_dense(rd, mode):
+    """Electric flows: f(e) = phi(u) - phi(v) against the dense potential, and Kirchhoff's
+    current law: the currents w_e f(e) out of every vertex sum to +1 at s, -1 at t, 0 elsewhere."""
+    g = F.random_connected(150, 400, 23, "lognormal")
+    s, t = F.random_pairs(g.n, 5, 8)
+    G = rd.Graph.from_csr(g)
+    f, r = G.flow(s, t, mode=mode, k_max=600, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6)
+    D = dense.DenseRD.of(g)
+    rows = g.rows()
+    tol = 1e-6 if mode == "fp64" else 1e-4
+    for p in range(len(s)):
+        phi = D.potential(int(s[p]), int(t[p]))
+        ref = phi[rows] - phi[g.col]
+        assert np.abs(f[p] - ref).max() < tol * np.abs(ref).max()
+        net = np.zeros(g.n)
+        np.add.at(net, rows, g.w.astype(np.float64) * f[p].astype(np.float64))
+        want = np.zeros(g.n)
+        want[s[p]] += 1.0
+        want[t[p]] -= 1.0
+        assert np.abs(net - want).max() < 10 * tol
+
+
+def test_power_method_matches_oracle_and_needs_more_steps(rd):
+    """Algorithm 1 on the GPU equals the FP64 oracle step by step; on a grid (large
+    condition number) it needs many times more steps than the Lanczos iteration to reach
+    relative error 1e-6 (the speed-up the paper reports for road networks)."""
+    g = F.grid_deleted(40, 0.05, 7)
+    s, t = F.random_pairs(g.n, 4, 9)
+    G = rd.Graph.from_csr(g)
+    steps = 3000
+    r, hist = G.power_method(s, t, steps, mode="fp64", history=True)
+    for p in range(2):
+        ref = power.power_method(g, int(s[p]), int(t[p]), steps)
+        assert np.abs(hist[:, p] - ref).max() < 1e-12 * np.abs(ref).max() + 1e-14
+    exact = dense.DenseRD.of(g).r(s, t)
+    lz = G.query(s, t, mode="fp64", k_max=2000, rel_tol=0.0, resid_tol=1e-12)
+    k_lz = np.array([np.argmax(np.abs(lanczos.lanczos_pair(g, int(a), int(b), 300)["r_hist"] / e - 1) <= 1e-6) + 1
+                     for a, b, e in zip(s, t, exact)])
+    rel_pm = np.abs(hist / exact[None, :] - 1)
+    k_pm = np.array([np.argmax(rel_pm[:, p] <= 1e-6) for p in range(len(s))])
+    assert np.all(rel_pm[-1] <= 1e-6)
+    assert np.all(k_pm > 5 * k_lz), (k_pm, k_lz)
+    assert rel(lz.r, exact).max() < 1e-9
+
+
+def test_triangle_weights_then_weighted_query(rd):
+    """Triangle-count weights (the weighted setting of the paper's experiments): each stored
+    entry gets the number of triangles through its edge (1 if none), as (A A) o A counts
+    them; the weighted query then matches the dense oracle on those weights."""
+    import scipy.sparse as sp
+
+    g, s, t = W.chunglu(5000, 2.1, 20.0, 50000, 8, 5)
+    G = rd.Graph.from_csr(g)
+    w = G.triangle_weights()
+    A = sp.csr_matrix((np.ones(g.nnz), g.col, g.row_ptr), shape=(g.n, g.n))
+    tri = (A @ A).multiply(A).tocsr()
+    tri.sort_indices()
+    ref = np.asarray(tri[g.rows(), g.col]).ravel()
+    ref = np.where(ref > 0, ref, 1.0)
+    assert np.array_equal(w, ref.astype(np.float32))
+    k = F.complete(6)
+    assert np.all(rd.Graph.from_csr(k).triangle_weights() == 4.0)      # K_6: n - 2 triangles per edge
+    gw = g.with_weights(w)
+    G.set_weights(w)
+    res = G.query(s, t, mode="fp64", rel_tol=0.0, resid_tol=1e-12)
+    assert rel(res.r, dense.DenseRD.of(gw).r(s, t)).max() < FP64_TOL

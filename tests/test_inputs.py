@@ -32,3 +32,9 @@ def test_csr_is_symmetric_simple_connected():
     from graphgen.graph import component_labels
 
     assert np.unique(component_labels(g)).size == 1
+
+
+def test_ba_c_generator_matches_python():
+    a = F.barabasi_albert(3000, 5, 9, fast=True)
+    b = F.barabasi_albert(3000, 5, 9, fast=False)
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)

@@ -15,7 +15,7 @@ import pytest
 
 from graphgen import families as F
 from graphgen.graph import to_csr
-from oracle import dense, lanczos
+from oracle import dense, lanczos, power
 from tests import closed_forms as CF
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -283,3 +283,26 @@ def test_planted_mistake_is_caught(name, tmp_path):
     so = str(tmp_path / f"lib{name}.so")
     subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", so, str(mut), "-lm"])
     assert not _pins_pass(lanczos.load(so)), f"planted mistake {name} passed every pin"
+
+
+# ------------------------------------------------------- Power Method part
+
+@pytest.mark.parametrize("make,s,t,ref", [
+    (lambda: F.complete(6), 0, 5, 2.0 / 6),
+    (lambda: F.cycle(10), 0, 4, CF.cycle_r(10, 4)),
+    (lambda: F.grid(6), 0, 35, CF.grid_r(6, 6, 0, 35)),
+])
+def test_power_method_converges_to_closed_forms(make, s, t, ref):
+    """Algorithm 1 is the series of Eq. (er_laylor_expansion): increasing partial sums
+    (each term is nonnegative) that converge to r."""
+    h = power.power_method(make(), s, t, 4000)
+    assert h[-1] == pytest.approx(ref, rel=1e-10)
+    assert np.all(np.diff(h) >= -1e-15)
+
+
+def test_power_method_first_terms_by_hand():
+    """Path 0-1-2 (degrees 1, 2, 1), s=0, t=2: r_0 = e_0 - e_2 gives term 1/2 + 1/2 = 1; then
+    r_1 = (I/2 + P/2) r_0 = [1/2, 0, -1/2] gives 1/4 + 1/4 = 1/2."""
+    h = power.power_method(F.path(3), 0, 2, 2)
+    assert h[0] == pytest.approx(1.0, abs=1e-15)
+    assert h[1] == pytest.approx(1.5, abs=1e-15)
