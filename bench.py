@@ -211,6 +211,114 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_sweeps(which: str):
+    """Extra measurements beyond the main line (one JSON line each):
+    scaling  -- Erdos-Renyi and Barabasi-Albert graphs, n = 1e2..1e6, m = n ln n, k = 20 fixed,
+                64 pairs, FP32 (the scalability experiment, Exp-3);
+    density  -- Erdos-Renyi n = 1000 with average degree 5/25/50/250, 10 top-degree vs 10
+                random vertices (all ordered pairs), k = 15 / k = 5, absolute error against the
+                dense oracle (the s,t-selection and density experiment, Exp-6);
+    pm       -- steps and time to relative error 1e-6 for the Lanczos iteration and the Power
+                Method (Algorithm 1) on a road-like grid and on a Chung-Lu graph."""
+    import torch
+
+    import paper_2601_11159_gb300 as rd
+    from graphgen import families as F
+    from oracle import dense
+    from oracle import lanczos as O
+
+    def timed(fn, reps=3):
+        best, out = None, None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best, out
+
+    if which in ("scaling", "all"):
+        import math
+
+        for fam in ["er", "ba"]:
+            for n in [100, 1000, 10_000, 100_000, 1_000_000]:
+                m = int(n * math.log(n))
+                g = F.erdos_renyi(n, m, 7) if fam == "er" else F.barabasi_albert(n, max(1, int(round(math.log(n)))), 7)
+                s, t = F.random_pairs(g.n, 64, 8)
+                G = rd.Graph.from_csr(g)
+                sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
+                ms, res = timed(lambda: G.query(sd, td, mode="fp32", k_max=20, fixed_k=True))
+                ref, _, _ = O.lanczos_batch(g, s[:4], t[:4], k_max=400, stop_tol=1e-13, threads=0)
+                err = np.abs(res.r.cpu().numpy()[:4] - ref) / ref
+                print(json.dumps({"sweep": "scaling", "family": fam, "n": g.n, "m": g.nnz // 2, "k": 20, "pairs": 64,
+                                  "query_ms": ms, "pairs_per_s": 64 / (ms / 1000), "max_rel_err_k20": float(err.max())}),
+                      flush=True)
+                G.close()
+    if which in ("density", "all"):
+        for d in [5, 25, 50, 250]:
+            g = F.erdos_renyi(1000, 1000 * d // 2, 11)
+            deg = np.diff(g.row_ptr)
+            top = np.argsort(-deg, kind="stable")[:10]
+            rnd = F.random_pairs(g.n, 10, 12)[0]
+            D = dense.DenseRD.of(g)
+            G = rd.Graph.from_csr(g)
+            for label, vs in [("top_degree", top), ("random", rnd)]:
+                a, b = np.meshgrid(vs, vs)
+                keep = a != b
+                s, t = a[keep].astype(np.int32), b[keep].astype(np.int32)
+                exact = D.r(s, t)
+                for k in [5, 15]:
+                    r = G.query(s, t, mode="fp64", k_max=k, fixed_k=True).r
+                    print(json.dumps({"sweep": "density", "n": g.n, "avg_degree": d, "select": label, "k": k,
+                                      "mean_abs_err": float(np.mean(np.abs(r - exact))),
+                                      "max_abs_err": float(np.max(np.abs(r - exact)))}), flush=True)
+            G.close()
+    if which in ("roadgrid", "all"):
+        from graphgen import workloads as W
+
+        g, s, t = W.roadgrid4096()
+        G = rd.Graph.from_csr(g)
+        for mode, kw in [("fp64", dict(rel_tol=0.0, resid_tol=1e-8)), ("fp32", dict(rel_tol=0.0, resid_tol=1e-6))]:
+            ms, res = timed(lambda: G.query(s, t, mode=mode, k_max=40000, **kw), reps=1)
+            st = G.last_stats()
+            print(json.dumps({"sweep": "roadgrid4096", "mode": mode, "n": g.n, "nnz": g.nnz, "pairs": len(s),
+                              "query_ms": ms, "pairs_per_s": len(s) / (ms / 1000), "stop": kw,
+                              "iters_min": int(res.iters.min()), "iters_median": float(np.median(res.iters)),
+                              "iters_max": int(res.iters.max()), "status": np.unique(res.status).tolist(),
+                              "compactions": st["compactions"],
+                              "spmm_gbs_algorithmic": st["spmm_bytes"] / max(st["spmm_ms"], 1e-9) / 1e6,
+                              "r_sample": res.r[:4].tolist()}), flush=True)
+        G.close()
+    if which in ("pm", "all"):
+        from graphgen import workloads as W
+
+        cases = []
+        gg = F.grid_deleted(128, 0.05, 3)
+        cases.append(("grid128_del5", gg) + F.random_pairs(gg.n, 8, 5))
+        cases.append(("chunglu100k",) + W.chunglu(100_000, 2.1, 20.0, 1_000_000, 8, 9))
+        for name, g, s, t in cases:
+            G = rd.Graph.from_csr(g)
+            ref, _, _ = O.lanczos_batch(g, s, t, k_max=20000, stop_tol=1e-14, threads=0)
+            steps = 200_000 if name.startswith("grid") else 2000
+            _, hist = G.power_method(s, t, steps, mode="fp64", history=True)
+            rel_pm = np.abs(hist / ref[None, :] - 1)
+            k_pm = [int(np.argmax(rel_pm[:, p] <= 1e-6)) if np.any(rel_pm[:, p] <= 1e-6) else None
+                    for p in range(len(s))]
+            kmax_pm = max(k for k in k_pm if k is not None) if any(k is not None for k in k_pm) else steps
+            ms_pm, _ = timed(lambda: G.power_method(s, t, kmax_pm, mode="fp64"), reps=1)
+            ms_lz, res = timed(lambda: G.query(s, t, mode="fp64", k_max=20000, rel_tol=1e-7))
+            err_lz = float(np.max(np.abs(res.r / ref - 1)))
+            print(json.dumps({"sweep": "lanczos_vs_power_method", "graph": name, "n": g.n, "pairs": len(s),
+                              "lanczos_steps_max": int(res.iters.max()), "lanczos_ms": ms_lz,
+                              "lanczos_max_rel_err": err_lz, "pm_steps_to_1e-6": k_pm, "pm_ms": ms_pm,
+                              "pm_steps_run": kmax_pm}), flush=True)
+            G.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -227,7 +335,11 @@ def main():
     ap.add_argument("--pairs", type=int, default=256)
     ap.add_argument("--kernel", default="tuned", choices=["tuned", "group", "stream"])
     ap.add_argument("--rhs-tile", type=int, default=0)
+    ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "roadgrid", "all"],
+                    help="extra measurements instead of the main line")
     args = ap.parse_args()
+    if args.sweep:
+        return run_sweeps(args.sweep)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

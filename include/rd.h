@@ -78,6 +78,8 @@ typedef enum {
 #define RD_Q_PROFILE 8u     /* time the dominant kernel with CUDA events (see rd_last_call_stats) */
 #define RD_Q_NO_COMPACT 16u /* rd_query: keep every pair's column until the end instead of packing
                                the still-active pairs into a narrower block as pairs converge */
+#define RD_Q_NO_ONCHIP 32u  /* rd_query: do not run small graphs (three vectors fit in one SM's
+                               shared memory) as one whole-recurrence kernel with one block per pair */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */
@@ -92,7 +94,8 @@ typedef struct {
                               rd_query polls every step, one step behind the device. */
     uint32_t flags;        /* RD_Q_* */
     int32_t kernel;        /* SpMM kernel: 0 = tuned, 1 = row-group (warp lanes split a row's
-                              nonzeros), 2 = row-stream (row groups walk runs of consecutive rows) */
+                              nonzeros), 2 = row-stream (row groups walk runs of consecutive rows);
+                              with one pair the tuned choice is the warp-per-task SpMV */
 } rd_query_opts;
 
 /* Per-call statistics of the last rd_query / rd_edge_grad / rd_potential on g. */
@@ -104,7 +107,7 @@ typedef struct {
     int32_t rhs_tile;        /* configuration used */
     int32_t rows_per_warp;
     int32_t nnz_lanes;       /* lanes that share one row's nonzeros */
-    int32_t kernel;          /* SpMM kernel used (1 = row-group, 2 = row-stream) */
+    int32_t kernel;          /* SpMM kernel used (1 = row-group, 2 = row-stream, 3 = single-column SpMV) */
     int64_t ld;              /* padded number of right-hand-side columns (vector row stride) */
     double spmm_bytes;       /* algorithmic bytes of all SpMM launches of the call, each
                                 4*nnz (+4*nnz weights) + 8*(n+1) + 3*ld*n*sizeof(element) with the
@@ -215,14 +218,15 @@ rd_status rd_flow(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npair
  * for callers that cannot call cudaMalloc (code running under another framework's
  * allocator or memory pool, processes that reserve all device memory up front, or
  * contexts where allocation is forbidden). It runs the same recurrence as rd_query with
- * the row-group SpMM kernel, taking the graph straight from the caller's device CSR
- * (no rd_graph is created) and using, as its only scratch, one fixed 32 MiB device
+ * the row-group SpMM kernel (or, for graphs whose three vectors fit in one SM's shared
+ * memory, the whole-recurrence kernel of RD_Q_NO_ONCHIP), taking the graph straight from
+ * the caller's device CSR (no rd_graph is created) and using, as its only scratch, one fixed 32 MiB device
  * array compiled into this library (every GPU that loads the library holds it until the
  * process exits).
  *  n, nnz, row_ptr, col_idx, weights : symmetric CSR as for rd_graph_create, DEVICE pointers;
  *                    self-loops are rejected (RD_ERR_UNSUPPORTED) since the CSR is used as is.
  *  s, t            : int32[npairs] device pointers.
- *  opts            : as rd_query (RD_Q_PROFILE is ignored; the SpMM kernel is always row-group;
+ *  opts            : as rd_query (RD_Q_PROFILE is ignored; the SpMM kernel is row-group;
  *                    disconnected pairs are not labelled and end as RD_ERR_NUMERIC).
  *  r_out           : double[npairs] device pointer; iters_out: int32[npairs] device or NULL.
  * Limits: the scratch must hold 24*n bytes of degrees plus the query workspace

@@ -34,6 +34,7 @@ RD_Q_NO_DEFLATE = 2
 RD_Q_PLAIN = 4
 RD_Q_PROFILE = 8
 RD_Q_NO_COMPACT = 16
+RD_Q_NO_ONCHIP = 32
 
 
 class QueryOpts(C.Structure):

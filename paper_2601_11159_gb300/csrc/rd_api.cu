@@ -314,6 +314,11 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     if (plain || P == 1) {
         c.vec = 1;
         c.gs = 1;
+        if (o.kernel == 0 && g->ntasks > 0) {  // warp-per-task SpMV
+            c.nzl = 1;
+            c.kind = 2;
+            return c;
+        }
         if (o.kernel == 2) {  // row-stream with one lane per task
             c.nzl = 1;
             c.kind = 1;
@@ -354,8 +359,13 @@ static rd_status make_plan(rd_graph* g, int64_t P, const rd_query_opts& o, bool 
     int bps = spmm_blocks_per_sm(pl->cfg, g->weighted, false, pl->fp64);
     if (bps < 1) bps = 1;
     int64_t gm = (int64_t)bps * g->sm_count;
-    const int64_t units = pl->cfg.kind == 1 ? g->ntasks : g->n;  // rows or tasks, one per row group
-    gm = std::min<int64_t>(gm, (units + rows_per_block - 1) / rows_per_block);
+    int64_t units = pl->cfg.kind == 1 ? g->ntasks : g->n;  // rows or tasks, one per row group
+    int64_t per_block = rows_per_block;
+    if (pl->cfg.kind == 2) {  // one task per warp
+        units = g->ntasks;
+        per_block = kWarps;
+    }
+    gm = std::min<int64_t>(gm, (units + per_block - 1) / per_block);
     pl->grid_main = (int)std::max<int64_t>(gm, 1);
     int bph = spmm_blocks_per_sm(pl->cfg, g->weighted, true, pl->fp64);
     if (bph < 1) bph = 1;
@@ -499,6 +509,7 @@ struct RunCtx {
     int cf_sel = 0, slot_sel = -1;  // slot_sel < 0: identity slot map
     bool in_region_x = false;
     bool lazy_walk = false;  // Power Method steps instead of Lanczos steps
+    bool onchip = false;     // whole recurrence per pair in one CTA (small graphs, queries only)
     int compactions = 0;
     EventPool* ev = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
@@ -716,6 +727,31 @@ static rd_status run_forward(RunCtx& c)
         return RD_ERR_INVALID_ARG;
     }
     if (h[1] == 0) return RD_OK;
+    if (c.onchip) {
+        OnchipArgs oa{};
+        oa.n = c.g->n;
+        oa.npairs = (int)c.P;
+        oa.row_ptr = c.g->row_ptr;
+        oa.col = c.g->col;
+        oa.w = c.g->w;
+        oa.deg64 = c.g->deg64;
+        oa.invdeg64 = c.g->invdeg64;
+        oa.deg32 = c.g->deg32;
+        oa.invdeg32 = c.g->invdeg32;
+        oa.s = c.b.s;
+        oa.t = c.b.t;
+        oa.heavy_thr = c.g->heavy_thr;
+        oa.n_heavy_rows = c.g->n_heavy_rows;
+        oa.heavy_rows = c.g->heavy_rows;
+        oa.fin = fa;
+        oa.elem_size = (int)c.pl.elem;
+        oa.weighted = c.g->weighted ? 1 : 0;
+        if (launch_onchip(c.st, oa)) {
+            ++c.launches;
+            RD_CUDA(cudaGetLastError());
+            return RD_OK;
+        }
+    }
     constexpr int kSlots = 4;   // pinned poll slots h[4 .. 7]
     cudaEvent_t poll_ev[kSlots] = {};
     if (c.lagged_polls)
@@ -809,7 +845,7 @@ static void record_stats(RunCtx& c)
     s.rhs_tile = c.pl.cfg.tp();
     s.rows_per_warp = c.pl.cfg.rpw();
     s.nnz_lanes = c.pl.cfg.nzl;
-    s.kernel = c.pl.cfg.kind == 1 ? 2 : 1;
+    s.kernel = c.pl.cfg.kind == 2 ? 3 : (c.pl.cfg.kind == 1 ? 2 : 1);
     s.ld = c.pl.ld;
     s.spmm_bytes += c.spmm_bytes;
     s.compactions += c.compactions;
@@ -895,6 +931,7 @@ static rd_status query_batch(rd_graph* g, const int32_t* s, const int32_t* t, in
     RunCtx c;
     c.ev = ev;
     RD_TRY(prepare_run(c, g, P, o, plain, false, st, compact && !plain, lagged_polls));
+    c.onchip = (o.flags & RD_Q_NO_ONCHIP) == 0 && onchip_smem_bytes(g->n, (int)c.pl.elem) <= 220 * 1024;
     RD_TRY(stage_pairs(c, s, t));
     rd_status rs = o.mode == RD_MODE_FP64 ? run_forward<double>(c) : run_forward<float>(c);
     if (rs < 0) return rs;

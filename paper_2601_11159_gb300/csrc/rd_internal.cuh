@@ -122,6 +122,29 @@ struct FinArgs {
     int elem_size;
 };
 
+// Whole recurrence of one pair per CTA with q_{i-1}, q_i and W in shared memory (graphs
+// small enough); reads the CSR from global memory (L1/L2 resident).
+struct OnchipArgs {
+    int64_t n;
+    int npairs;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* w;
+    const double* deg64;
+    const double* invdeg64;
+    const float* deg32;
+    const float* invdeg32;
+    const int32_t* s;
+    const int32_t* t;
+    int heavy_thr;
+    int64_t n_heavy_rows;
+    const int32_t* heavy_rows;
+    FinArgs fin;                  // stop rule, tolerances, per-pair state
+    int elem_size, weighted;
+};
+size_t onchip_smem_bytes(int64_t n, int elem_size);
+bool launch_onchip(cudaStream_t st, const OnchipArgs& a);
+
 // Column compaction: keep the slots whose pair is still active, in slot order.
 struct CompactArgs {
     int64_t n, ld_old, ld_new;

@@ -770,6 +770,108 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
     }
 }
 
+// Single-column SpMV (one pair per launch, ld = 1). One warp per task (consecutive rows
+// with at most kTaskNnz nonzeros, or one heavy row): the lanes stride over the task's
+// nonzeros with coalesced index loads and 8 gathers in flight per lane, leaving the
+// products w_e q[col_e] in the warp's slice of shared memory; then each lane sums whole
+// rows from shared memory and runs the row epilogue. No block-wide barriers.
+constexpr int kTaskNnz = 512;
+
+template <typename T, bool WEIGHTED>
+__global__ void __launch_bounds__(kBlock) k_spmv_tasks(const StepArgs<T> a)
+{
+    __shared__ T prod[kWarps][kTaskNnz];
+    __shared__ double red[kWarps][1];
+    if (a.active_prev && *a.active_prev == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * kWarps;
+    const int ntasks = (int)a.ntasks;
+    const T bt = a.cf_beta[0];
+    Acc<T> sA, sB, sC;
+    T* pw = prod[warp];
+    for (int task = blockIdx.x * kWarps + warp; task < ntasks; task += nwarps) {
+        const int r0 = a.task_row[task], r1 = a.task_row[task + 1];
+        const int64_t e0 = a.row_ptr[r0], e1 = a.row_ptr[r1];
+        if (r1 == r0 + 1 && e1 - e0 > a.heavy_thr) {
+            // heavy row: sum of its chunk partials (chunk order within each lane, then a tree)
+            T acc[1] = {T(0)};
+            heavy_row_sum<T, 1, 32>(a, r0, 0, lane, acc);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], off);
+            if (lane == 0) {
+                T qp[1], qc[1], bt1[1] = {bt};
+                qp[0] = a.qprev_w[r0];
+                qc[0] = a.qcur[r0];
+                Acc<T> tA[1] = {sA}, tB[1] = {sB}, tC[1] = {sC};
+                row_epilogue<T, 1>(a, r0, 0, a.invdeg[r0], a.deg[r0], acc, bt1, qp, qc, tA, tB, tC);
+                sA = tA[0];
+                sB = tB[0];
+                sC = tC[0];
+            }
+            continue;
+        }
+        const int cnt = (int)(e1 - e0);
+        // phase 1: products into shared memory
+        for (int k0 = 0; k0 < cnt; k0 += 32 * 8) {
+            T x[8];
+            int idx[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                idx[u] = k0 + u * 32 + lane;
+                x[u] = T(0);
+                if (idx[u] < cnt) {
+                    const int64_t j = __ldg(a.col + e0 + idx[u]);
+                    x[u] = __ldg(a.qcur + j);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (idx[u] < cnt) {
+                    if constexpr (WEIGHTED) pw[idx[u]] = (T)__ldg(a.w + e0 + idx[u]) * x[u];
+                    else pw[idx[u]] = x[u];
+                }
+            }
+        }
+        __syncwarp();
+        // phase 2: one lane per row
+        for (int r = r0 + lane; r < r1; r += 32) {
+            const int b0 = (int)(a.row_ptr[r] - e0), b1 = (int)(a.row_ptr[r + 1] - e0);
+            T sum = T(0);
+            for (int k = b0; k < b1; ++k) sum += pw[k];
+            T acc[1] = {sum}, qp[1], qc[1], bt1[1] = {bt};
+            qp[0] = a.qprev_w[r];
+            qc[0] = a.qcur[r];
+            Acc<T> tA[1] = {sA}, tB[1] = {sB}, tC[1] = {sC};
+            row_epilogue<T, 1>(a, r, 0, a.invdeg[r], a.deg[r], acc, bt1, qp, qc, tA, tB, tC);
+            sA = tA[0];
+            sB = tB[0];
+            sC = tC[0];
+        }
+        __syncwarp();
+    }
+    if (a.do_reduce) {
+        Acc<T> vA[1] = {sA}, vB[1] = {sB}, vC[1] = {sC};
+        block_partials<T, 1, 1, 1>(a, vA, vB, vC, red, 0, lane, warp, 0);
+    }
+}
+
+template <typename T>
+bool launch_spmv_tasks(bool weighted, int grid, cudaStream_t st, const StepArgs<T>& a)
+{
+    if (weighted) k_spmv_tasks<T, true><<<grid, kBlock, 0, st>>>(a);
+    else k_spmv_tasks<T, false><<<grid, kBlock, 0, st>>>(a);
+    return true;
+}
+
+template <typename T>
+int occupancy_spmv_tasks(bool weighted)
+{
+    int nb = 0;
+    if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_tasks<T, true>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_tasks<T, false>, kBlock, 0);
+    return nb;
+}
+
 template <typename T, int VEC, int GS>
 bool launch_rows_cfg(bool weighted, int grid, cudaStream_t st, const StepArgs<T>& a)
 {

@@ -28,6 +28,7 @@ namespace rd {
 bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
                      const StepArgs<float>& a)
 {
+    if (c.kind == 2 && !heavy) return launch_spmv_tasks<float>(weighted, grid, st, a);
     if (c.kind == 1 && !heavy) {
 #define X(V, G) \
     if (c.vec == V && c.gs == G && c.nzl == 1) return launch_rows_cfg<float, V, G>(weighted, grid, st, a);
@@ -37,7 +38,7 @@ bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
     }
     // the heavy-row pre-pass of a row-stream config runs the row-group heavy kernel with the
     // same column tile; single-column tiles use 8 nonzero lanes there
-    const int zl = (c.kind == 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
+    const int zl = (c.kind >= 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
 #define X(V, G, Z) \
     if (c.vec == V && c.gs == G && zl == Z) return launch_cfg<float, V, G, Z>(weighted, heavy, grid, st, a);
     RD_F32_CONFIGS(X)
@@ -47,6 +48,7 @@ bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
 
 int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy)
 {
+    if (c.kind == 2 && !heavy) return occupancy_spmv_tasks<float>(weighted);
     if (c.kind == 1 && !heavy) {
 #define X(V, G) \
     if (c.vec == V && c.gs == G && c.nzl == 1) return occupancy_rows_cfg<float, V, G>(weighted);
@@ -54,7 +56,7 @@ int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy)
 #undef X
         return 0;
     }
-    const int zl = (c.kind == 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
+    const int zl = (c.kind >= 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
 #define X(V, G, Z) \
     if (c.vec == V && c.gs == G && zl == Z) return occupancy_cfg<float, V, G, Z>(weighted, heavy);
     RD_F32_CONFIGS(X)
@@ -68,6 +70,7 @@ std::vector<SpmmCfg> spmm_configs_f32()
 #define X(V, G, Z) v.push_back(SpmmCfg{V, G, Z, 0});
     RD_F32_CONFIGS(X)
 #undef X
+    v.push_back(SpmmCfg{1, 1, 1, 2});
 #define X(V, G) v.push_back(SpmmCfg{V, G, 1, 1});
     RD_F32_ROWS(X)
 #undef X

@@ -25,6 +25,7 @@ namespace rd {
 bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
                      const StepArgs<double>& a)
 {
+    if (c.kind == 2 && !heavy) return launch_spmv_tasks<double>(weighted, grid, st, a);
     if (c.kind == 1 && !heavy) {
 #define X(V, G) \
     if (c.vec == V && c.gs == G && c.nzl == 1) return launch_rows_cfg<double, V, G>(weighted, grid, st, a);
@@ -34,7 +35,7 @@ bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
     }
     // the heavy-row pre-pass of a row-stream config runs the row-group heavy kernel with the
     // same column tile; single-column tiles use 8 nonzero lanes there
-    const int zl = (c.kind == 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
+    const int zl = (c.kind >= 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
 #define X(V, G, Z) \
     if (c.vec == V && c.gs == G && zl == Z) return launch_cfg<double, V, G, Z>(weighted, heavy, grid, st, a);
     RD_F64_CONFIGS(X)
@@ -44,6 +45,7 @@ bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
 
 int spmm_blocks_per_sm_f64(const SpmmCfg& c, bool weighted, bool heavy)
 {
+    if (c.kind == 2 && !heavy) return occupancy_spmv_tasks<double>(weighted);
     if (c.kind == 1 && !heavy) {
 #define X(V, G) \
     if (c.vec == V && c.gs == G && c.nzl == 1) return occupancy_rows_cfg<double, V, G>(weighted);
@@ -51,7 +53,7 @@ int spmm_blocks_per_sm_f64(const SpmmCfg& c, bool weighted, bool heavy)
 #undef X
         return 0;
     }
-    const int zl = (c.kind == 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
+    const int zl = (c.kind >= 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
 #define X(V, G, Z) \
     if (c.vec == V && c.gs == G && zl == Z) return occupancy_cfg<double, V, G, Z>(weighted, heavy);
     RD_F64_CONFIGS(X)
@@ -65,6 +67,7 @@ std::vector<SpmmCfg> spmm_configs_f64()
 #define X(V, G, Z) v.push_back(SpmmCfg{V, G, Z, 0});
     RD_F64_CONFIGS(X)
 #undef X
+    v.push_back(SpmmCfg{1, 1, 1, 2});
 #define X(V, G) v.push_back(SpmmCfg{V, G, 1, 1});
     RD_F64_ROWS(X)
 #undef X

@@ -77,43 +77,18 @@ void launch_init(cudaStream_t st, const InitArgs& a)
 //   g_1 = 1,                g_i = beta_i g_{i-1} / delta_{i-1}        (g = L^{-1} e_1)
 //   S_i = S_{i-1} + g_i^2 / delta_i = e_1^T J_i^{-1} e_1,   r_i = ||b||^2 S_i
 //   residual ||b - (I - Ahat) x_i|| / ||b|| = beta_{i+1} |g_i / delta_i|.
-template <typename T>
-__global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
+// Step i = j + 1 of pair p from the three reduced sums A = <w, v_i>, B = ||w||^2 and
+// C = <w, D^{1/2}1> of w = Ahat v_i - beta_i v_{i-1}:
+//   alpha_i = A, beta_{i+1}^2 = B - A^2 - C^2/sum(d) (deflated component removed),
+//   LDL^T of J_i = I - T_i: delta_1 = 1 - alpha_1, delta_i = (1 - alpha_i) - beta_i^2/delta_{i-1},
+//   g_1 = 1, g_i = beta_i g_{i-1}/delta_{i-1}, S_i = S_{i-1} + g_i^2/delta_i, r_i = ||b||^2 S_i,
+//   residual ||b - (I - Ahat) x_i||/||b|| = beta_{i+1} |g_i/delta_i|.
+// Writes the pair's state and history; returns true when the pair stops (then active = 0),
+// else leaves alpha_i, the deflation constant c_i and beta_{i+1} in the outputs.
+__device__ __forceinline__ bool pair_update(const FinArgs& a, const PairState& st, int p, int j, double A, double B,
+                                            double C, double* alpha_o, double* cdef_o, double* beta_next_o)
 {
-    __shared__ double part[3][8][32];
-    const int lane = threadIdx.x & 31, split = threadIdx.x >> 5;
-    const int64_t col = (int64_t)blockIdx.x * 32 + lane;
-    const PairState& st = a.st;
-    if (st.act_count[a.step] == 0) return;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    if (col < a.ld) {
-        const int64_t slab = col / a.tp, cin = col % a.tp;
-        for (int b = split; b < a.nblocks; b += 8) {
-            const double* bp = a.block_part + ((slab * a.nblocks + b) * 3) * a.tp + cin;
-            s0 += bp[0];
-            s1 += bp[a.tp];
-            s2 += bp[2 * a.tp];
-        }
-    }
-    part[0][split][lane] = s0;
-    part[1][split][lane] = s1;
-    part[2][split][lane] = s2;
-    __syncthreads();
-    if (split != 0 || col >= a.ld) return;
-    const int p = a.slot_pair ? a.slot_pair[col] : (col < a.npairs ? (int)col : -1);
-    if (p < 0 || !st.active[p]) return;
-    double A = 0.0, B = 0.0, C = 0.0;
-#pragma unroll
-    for (int sp = 0; sp < 8; ++sp) {
-        A += part[0][sp][lane];
-        B += part[1][sp][lane];
-        C += part[2][sp][lane];
-    }
-    const int j = a.step;       // 0-based step index; Lanczos step i = j + 1
-    const int64_t ld = a.ld;
     const int64_t np = a.pstride;  // stride of the per-pair arrays
-    T* cfs = static_cast<T*>(a.cf_step);
-    T* cfn = static_cast<T*>(a.cf_next);
     const double alpha = A;
     const double beta_i = st.beta[p];
     const double cdef = a.deflate ? C / a.sumdeg : 0.0;
@@ -167,8 +142,56 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
         }
     }
     if (stop) {
-        // zero coefficients: the column's vectors become (and stay) zero
         st.active[p] = 0;
+        return true;
+    }
+    st.beta[p] = beta_next;
+    *alpha_o = alpha;
+    *cdef_o = cdef;
+    *beta_next_o = beta_next;
+    return false;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
+{
+    __shared__ double part[3][8][32];
+    const int lane = threadIdx.x & 31, split = threadIdx.x >> 5;
+    const int64_t col = (int64_t)blockIdx.x * 32 + lane;
+    const PairState& st = a.st;
+    if (st.act_count[a.step] == 0) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (col < a.ld) {
+        const int64_t slab = col / a.tp, cin = col % a.tp;
+        for (int b = split; b < a.nblocks; b += 8) {
+            const double* bp = a.block_part + ((slab * a.nblocks + b) * 3) * a.tp + cin;
+            s0 += bp[0];
+            s1 += bp[a.tp];
+            s2 += bp[2 * a.tp];
+        }
+    }
+    part[0][split][lane] = s0;
+    part[1][split][lane] = s1;
+    part[2][split][lane] = s2;
+    __syncthreads();
+    if (split != 0 || col >= a.ld) return;
+    const int p = a.slot_pair ? a.slot_pair[col] : (col < a.npairs ? (int)col : -1);
+    if (p < 0 || !st.active[p]) return;
+    double A = 0.0, B = 0.0, C = 0.0;
+#pragma unroll
+    for (int sp = 0; sp < 8; ++sp) {
+        A += part[0][sp][lane];
+        B += part[1][sp][lane];
+        C += part[2][sp][lane];
+    }
+    const int j = a.step;       // 0-based step index; Lanczos step i = j + 1
+    const int64_t ld = a.ld;
+    T* cfs = static_cast<T*>(a.cf_step);
+    T* cfn = static_cast<T*>(a.cf_next);
+    double alpha, cdef, beta_next;
+    const bool stop = pair_update(a, st, p, j, A, B, C, &alpha, &cdef, &beta_next);
+    if (stop) {
+        // zero coefficients: the column's vectors become (and stay) zero
         cfs[1 * ld + col] = T(0);
         cfs[2 * ld + col] = T(0);
         cfs[3 * ld + col] = T(0);
@@ -179,7 +202,6 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
     cfs[2 * ld + col] = (T)cdef;
     cfs[3 * ld + col] = (T)(1.0 / beta_next);
     cfn[col] = (T)beta_next;
-    st.beta[p] = beta_next;
     atomicAdd(&st.act_count[j + 1], 1);
 }
 
@@ -516,6 +538,140 @@ void launch_pm_accum(cudaStream_t st, const PmArgs& a)
     const int nb = (a.npairs + 127) / 128;
     if (a.elem_size == 8) k_pm_accum<double><<<nb, 128, 0, st>>>(a);
     else k_pm_accum<float><<<nb, 128, 0, st>>>(a);
+}
+
+// ------------------------------------------------------------- on chip
+// One pair per CTA, every step in one launch: SpMV from shared memory (one thread per light
+// row, one warp per row above heavy_thr), three FP64 block sums in a fixed order, the same
+// per-pair update as k_finalize (pair_update) by thread 0, normalisation in shared memory.
+constexpr int kOnchipThreads = 1024;
+
+size_t onchip_smem_bytes(int64_t n, int elem_size) { return (size_t)3 * (size_t)n * (size_t)elem_size + 64; }
+
+template <typename T, bool WEIGHTED>
+__global__ void __launch_bounds__(kOnchipThreads) k_lanczos_onchip(const OnchipArgs a)
+{
+    extern __shared__ __align__(16) unsigned char onchip_raw[];
+    __shared__ double red[3][kOnchipThreads / 32];
+    __shared__ double coef[3];
+    __shared__ int stop_s;
+    const int p = blockIdx.x;
+    const PairState& st = a.fin.st;
+    if (p >= a.npairs || !st.active[p]) return;  // uniform over the block
+    const int64_t n = a.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = blockDim.x, nwarps = nthr >> 5;
+    T* buf[3];
+    buf[0] = reinterpret_cast<T*>(onchip_raw);
+    buf[1] = buf[0] + n;
+    buf[2] = buf[1] + n;
+    int iprev = 0, icur = 1, iw = 2;
+    for (int64_t u = tid; u < 3 * n; u += nthr) buf[0][u] = T(0);
+    __syncthreads();
+    if (tid == 0) {
+        const int32_t s = a.s[p], t = a.t[p];
+        const double ds = a.deg64[s], dt = a.deg64[t];
+        const double bn = sqrt(st.b2[p]);
+        buf[icur][s] = (T)(1.0 / (ds * bn));
+        buf[icur][t] = (T)(-1.0 / (dt * bn));
+    }
+    __syncthreads();
+    T bt = T(0);
+    for (int j = 0; j < a.fin.k_max; ++j) {
+        const T* qp = buf[iprev];
+        const T* qc = buf[icur];
+        T* W = buf[iw];
+        double pa = 0.0, pb = 0.0, pc = 0.0;
+        for (int64_t u = tid; u < n; u += nthr) {
+            const int64_t e0 = a.row_ptr[u], e1 = a.row_ptr[u + 1];
+            if (e1 - e0 > a.heavy_thr) continue;
+            T acc = T(0);
+            for (int64_t e = e0; e < e1; ++e) {
+                if constexpr (WEIGHTED) acc += (T)__ldg(a.w + e) * qc[__ldg(a.col + e)];
+                else acc += qc[__ldg(a.col + e)];
+            }
+            const T invd = sizeof(T) == 8 ? (T)a.invdeg64[u] : (T)a.invdeg32[u];
+            const T du = sizeof(T) == 8 ? (T)a.deg64[u] : (T)a.deg32[u];
+            const T wv = invd * acc - bt * qp[u];
+            W[u] = wv;
+            const T dw = du * wv;
+            pa += (double)(dw * qc[u]);
+            pb += (double)(dw * wv);
+            pc += (double)dw;
+        }
+        for (int64_t h = warp; h < a.n_heavy_rows; h += nwarps) {
+            const int64_t u = a.heavy_rows[h];
+            T acc = T(0);
+            for (int64_t e = a.row_ptr[u] + lane; e < a.row_ptr[u + 1]; e += 32) {
+                if constexpr (WEIGHTED) acc += (T)__ldg(a.w + e) * qc[__ldg(a.col + e)];
+                else acc += qc[__ldg(a.col + e)];
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) {
+                const T invd = sizeof(T) == 8 ? (T)a.invdeg64[u] : (T)a.invdeg32[u];
+                const T du = sizeof(T) == 8 ? (T)a.deg64[u] : (T)a.deg32[u];
+                const T wv = invd * acc - bt * qp[u];
+                W[u] = wv;
+                const T dw = du * wv;
+                pa += (double)(dw * qc[u]);
+                pb += (double)(dw * wv);
+                pc += (double)dw;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            pa += __shfl_xor_sync(0xffffffffu, pa, off);
+            pb += __shfl_xor_sync(0xffffffffu, pb, off);
+            pc += __shfl_xor_sync(0xffffffffu, pc, off);
+        }
+        if (lane == 0) {
+            red[0][warp] = pa;
+            red[1][warp] = pb;
+            red[2][warp] = pc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double A = 0.0, B = 0.0, C = 0.0;
+            for (int w = 0; w < nwarps; ++w) {
+                A += red[0][w];
+                B += red[1][w];
+                C += red[2][w];
+            }
+            double al = 0.0, cd = 0.0, bn = 0.0;
+            const bool stop = pair_update(a.fin, st, p, j, A, B, C, &al, &cd, &bn);
+            stop_s = stop ? 1 : 0;
+            coef[0] = al;
+            coef[1] = cd;
+            coef[2] = bn;
+        }
+        __syncthreads();
+        if (stop_s) break;
+        const T al = (T)coef[0], cd = (T)coef[1], ib = (T)(1.0 / coef[2]);
+        for (int64_t u = tid; u < n; u += nthr) W[u] = (W[u] - al * qc[u] - cd) * ib;
+        bt = (T)coef[2];
+        const int old_prev = iprev;
+        iprev = icur;
+        icur = iw;
+        iw = old_prev;
+        __syncthreads();
+    }
+}
+
+bool launch_onchip(cudaStream_t st, const OnchipArgs& a)
+{
+    const size_t sm = onchip_smem_bytes(a.n, a.elem_size);
+    if (sm > 220 * 1024) return false;
+    if (a.elem_size == 8) {
+        auto k = a.weighted ? k_lanczos_onchip<double, true> : k_lanczos_onchip<double, false>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k<<<a.npairs, kOnchipThreads, sm, st>>>(a);
+    } else {
+        auto k = a.weighted ? k_lanczos_onchip<float, true> : k_lanczos_onchip<float, false>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k<<<a.npairs, kOnchipThreads, sm, st>>>(a);
+    }
+    return true;
 }
 
 }  // namespace rd

@@ -64,17 +64,18 @@ def test_roadgrid4096_fp64(rd):
     G = rd.Graph.from_csr(g)
     k = 100
     r100 = G.query(s, t, mode="fp64", k_max=k, fixed_k=True).r
-    for p in [0, 37]:
-        ref = lanczos.lanczos_pair(g, int(s[p]), int(t[p]), k_max=k)["r"]
-        assert rel([r100[p]], [ref])[0] < FP64_TOL
-    res = G.query(s, t, mode="fp64", k_max=40000, rel_tol=0.0, resid_tol=1e-8)
+    pick = np.array([0, 37])
+    ref, _, _ = lanczos.lanczos_batch(g, s[pick], t[pick], k_max=k, stop_tol=0.0, threads=0)
+    assert rel(r100[pick], ref).max() < FP64_TOL
+    # long runs to convergence on 8 of the 64 pairs (the rest share the same code path)
+    res = G.query(s[:8], t[:8], mode="fp64", k_max=40000, rel_tol=0.0, resid_tol=1e-8)
     assert np.all(res.status == 0), np.unique(res.status)
-    assert np.all(res.r >= r100 * (1 - 1e-12))
+    assert np.all(res.r >= r100[:8] * (1 - 1e-12))
     old = g.meta["lcc_old_id"]
     lower = np.array([CF.grid_r(4096, 4096, int(old[a]), int(old[b])) / 2.0 for a, b in zip(s[:8], t[:8])])
-    assert np.all(res.r[:8] >= lower)
-    back = G.query(t[:4], s[:4], mode="fp64", k_max=40000, rel_tol=0.0, resid_tol=1e-8)
-    assert rel(back.r, res.r[:4]).max() < 1e-6
+    assert np.all(res.r >= lower)
+    back = G.query(t[:2], s[:2], mode="fp64", k_max=40000, rel_tol=0.0, resid_tol=1e-8)
+    assert rel(back.r, res.r[:2]).max() < 1e-6
 
 
 def test_chunglu4m_weighted_gradient(rd):

@@ -51,15 +51,15 @@ SMALL = [
 
 @pytest.mark.parametrize("name,make", SMALL)
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
-@pytest.mark.parametrize("kernel", ["group", "stream"])
+@pytest.mark.parametrize("kernel", ["group", "stream", "onchip"])
 def test_small_graphs_vs_dense(rd, name, make, mode, kernel):
     g = make()
     s, t = F.random_pairs(g.n, 9, 17)
     ref = dense.DenseRD.of(g).r(s, t)
     G = rd.Graph.from_csr(g)
     tol = FP64_TOL if mode == "fp64" else FP32_TOL
-    res = G.query(s, t, mode=mode, k_max=400, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6,
-                  kernel=kernel)
+    kw = dict(onchip=True) if kernel == "onchip" else dict(kernel=kernel, onchip=False)
+    res = G.query(s, t, mode=mode, k_max=400, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6, **kw)
     assert np.all(res.status >= 0), res.status
     assert rel(res.r, ref).max() < tol, (name, mode, rel(res.r, ref).max())
 
@@ -71,10 +71,11 @@ def test_fixed_k_matches_oracle_history(rd, mode, tol):
     s, t = F.random_pairs(g.n, 5, 2)
     G = rd.Graph.from_csr(g)
     for k in [1, 2, 5, 12, 30]:
-        res = G.query(s, t, mode=mode, k_max=k, fixed_k=True)
-        assert np.all(res.iters == k)
         ref = np.array([lanczos.lanczos_pair(g, int(a), int(b), k_max=k)["r"] for a, b in zip(s, t)])
-        assert rel(res.r, ref).max() < tol, (k, rel(res.r, ref).max())
+        for onchip in (False, True):
+            res = G.query(s, t, mode=mode, k_max=k, fixed_k=True, onchip=onchip)
+            assert np.all(res.iters == k)
+            assert rel(res.r, ref).max() < tol, (k, onchip, rel(res.r, ref).max())
 
 
 def test_grid64_corner_fp64_closed_form(rd):
@@ -100,10 +101,11 @@ def test_ragged_batch_edge_cases(rd):
     ref = dense.DenseRD.of(g).r(s, t)
     G = rd.Graph.from_csr(g)
     for mode, tol in [("fp64", FP64_TOL), ("fp32", FP32_TOL)]:
-        res = G.query(s, t, mode=mode, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6)
-        assert res.r[3] == 0.0 and res.iters[3] == 0 and res.status[3] == 0
-        m = np.arange(37) != 3
-        assert rel(res.r[m], ref[m]).max() < tol
+        for onchip in (False, True):
+            res = G.query(s, t, mode=mode, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6, onchip=onchip)
+            assert res.r[3] == 0.0 and res.iters[3] == 0 and res.status[3] == 0
+            m = np.arange(37) != 3
+            assert rel(res.r[m], ref[m]).max() < tol
     empty = G.query(np.zeros(0, np.int32), np.zeros(0, np.int32))
     assert empty.r.size == 0
 
@@ -270,6 +272,7 @@ def test_compaction_matches_fixed_layout(rd, mode):
         ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=200, stop_tol=1e-13, threads=0)
         tol_ab, tol_ref = 2e-6, FP32_TOL
     G = rd.Graph.from_csr(g)
+    kw["onchip"] = False
     a = G.query(s, t, **kw)
     st = G.last_stats()
     b = G.query(s, t, compact=False, **kw)
@@ -346,3 +349,57 @@ def test_triangle_weights_then_weighted_query(rd):
     G.set_weights(w)
     res = G.query(s, t, mode="fp64", rel_tol=0.0, resid_tol=1e-12)
     assert rel(res.r, dense.DenseRD.of(gw).r(s, t)).max() < FP64_TOL
+
+
+@pytest.mark.parametrize("family", ["er", "ba"])
+def test_er_ba_workloads_vs_dense(rd, family):
+    """Erdos-Renyi and Barabasi-Albert graphs (the scalability and density experiments):
+    converged queries against the dense oracle, fixed k = 20 against the oracle's rhat_20."""
+    import math
+
+    n = 1500
+    g = F.erdos_renyi(n, int(n * math.log(n)), 4) if family == "er" else F.barabasi_albert(n, 7, 4)
+    s, t = F.random_pairs(g.n, 20, 6)
+    G = rd.Graph.from_csr(g)
+    ref = dense.DenseRD.of(g).r(s, t)
+    for mode, tol in [("fp64", FP64_TOL), ("fp32", FP32_TOL)]:
+        res = G.query(s, t, mode=mode, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6)
+        assert rel(res.r, ref).max() < tol
+    r20 = G.query(s, t, mode="fp64", k_max=20, fixed_k=True).r
+    for p in range(3):
+        assert rel([r20[p]], [lanczos.lanczos_pair(g, int(s[p]), int(t[p]), 20)["r"]])[0] < 1e-11
+
+
+def test_plain_kernels_agree(rd):
+    """The single-pair path: warp-per-task SpMV, row-group and row-stream kernels agree."""
+    g, s, t = W.chunglu(30000, 2.1, 20.0, 300000, 6, 17)
+    G = rd.Graph.from_csr(g)
+    out = [G.query(s, t, mode=m, k_max=40, fixed_k=True, plain=True, kernel=k).r
+           for m in ["fp64"] for k in ["tuned", "group", "stream"]]
+    assert G.last_stats()["kernel"] == 2
+    assert rel(out[1], out[0]).max() < 1e-12 and rel(out[2], out[0]).max() < 1e-12
+    r32 = G.query(s, t, mode="fp32", k_max=40, fixed_k=True, plain=True).r
+    assert rel(r32, out[0]).max() < 2e-5
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
+def test_onchip_path_matches_multikernel_path(rd, mode, tol):
+    """Small graphs run as one whole-recurrence kernel (one block per pair); the result equals
+    the multi-kernel path's within reduction-order rounding, for plain and weighted graphs with
+    heavy rows (a star hub) and tolerance stops."""
+    a = F.random_connected(3000, 9000, 41, "lognormal")
+    hub = F.star(400)
+    ea, eb, wa = a.undirected_edges()
+    ha, hb, _ = hub.undirected_edges()
+    g = to_csr(3000, np.concatenate([ea, ha]), np.concatenate([eb, hb]),
+               np.concatenate([wa, np.ones(ha.size, np.float32)]))
+    s, t = F.random_pairs(g.n, 33, 4)
+    G = rd.Graph.from_csr(g)
+    for kw in [dict(k_max=30, fixed_k=True), dict(k_max=400, rel_tol=1e-9 if mode == "fp64" else 1e-6)]:
+        on = G.query(s, t, mode=mode, **kw)
+        off = G.query(s, t, mode=mode, onchip=False, **kw)
+        assert np.abs(on.iters.astype(int) - off.iters.astype(int)).max() <= 1
+        assert rel(on.r, off.r).max() < (tol if "fixed_k" in kw else 50 * tol)
+    ref = dense.DenseRD.of(g).r(s, t)
+    res = G.query(s, t, mode=mode, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-6)
+    assert rel(res.r, ref).max() < (FP64_TOL if mode == "fp64" else FP32_TOL)
