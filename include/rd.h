@@ -80,6 +80,9 @@ typedef enum {
                                the still-active pairs into a narrower block as pairs converge */
 #define RD_Q_NO_ONCHIP 32u  /* rd_query: do not run small graphs (three vectors fit in one SM's
                                shared memory) as one whole-recurrence kernel with one block per pair */
+#define RD_Q_NO_TUNE 64u    /* with rhs_tile, rows_per_warp and kernel all 0: pick the SpMM
+                               configuration by a fixed rule instead of the autotuner (see
+                               rd_autotune) */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */
@@ -113,6 +116,7 @@ typedef struct {
                                 4*nnz (+4*nnz weights) + 8*(n+1) + 3*ld*n*sizeof(element) with the
                                 ld in force at that launch (it shrinks as converged pairs are packed) */
     int32_t compactions;     /* times the active pairs were packed into a narrower block */
+    int32_t tuned;           /* 1 if the configuration came from the autotuner's table */
 } rd_call_stats;
 
 /* Fill `opts` with defaults: k_max 1000, rel_tol 1e-7, resid_tol 0, FP32 vectors with FP64
@@ -241,6 +245,28 @@ rd_status rd_flow(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npair
 rd_status rd_query_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                            const float* weights, const int32_t* s, const int32_t* t, int64_t npairs,
                            const rd_query_opts* opts, double* r_out, int32_t* iters_out, void* stream);
+
+/* SpMM autotuner. No counterpart in the paper: it picks the right-hand-side tile, the rows
+ * per warp and the kernel of the SpMM step (Algorithm 3, line 3) for this graph and GPU by
+ * timing, not by a fixed rule. For a query of npairs pairs in opts->mode it times every
+ * instantiated candidate (tiles from a quarter of the pair count's power-of-two width up to
+ * that width; the row-stream kernel and the row-group kernel with 1, 2 or 4 nonzero lanes
+ * per row group; for one column the warp-per-task SpMV, the row-stream and the row-group
+ * SpMV) on g's own CSR with zeroed vectors, one warm-up and three timed launches each (CUDA
+ * events on `stream`), and keeps the fastest per width class in g. Without RD_Q_PLAIN (and
+ * npairs > 1) the narrower classes a compacting query passes through are tuned as well,
+ * unless RD_Q_NO_COMPACT is set. Calls on g whose opts leave rhs_tile, rows_per_warp and
+ * kernel at 0 without RD_Q_NO_TUNE use the table, and tune a missing class on first use.
+ *  npairs  : 1 .. 2^24.
+ *  opts    : mode and flags as for rd_query (NULL = defaults); rhs_tile, rows_per_warp and
+ *            kernel must be 0 and RD_Q_NO_TUNE unset, else RD_ERR_INVALID_ARG.
+ *  rhs_tile_out, rows_per_warp_out, kernel_out : nullable; the configuration a query of
+ *            npairs pairs now starts with (kernel numbered as in rd_call_stats).
+ * Uses (and may grow) g's workspace; the GPU work is on `stream`, which is synchronised
+ * before return. Returns RD_OK, RD_ERR_INVALID_ARG, RD_ERR_CUDA or RD_ERR_OOM (a candidate
+ * whose workspace does not fit is skipped; RD_ERR_OOM only if none fits). */
+rd_status rd_autotune(rd_graph* g, int64_t npairs, const rd_query_opts* opts, int32_t* rhs_tile_out,
+                      int32_t* rows_per_warp_out, int32_t* kernel_out, void* stream);
 
 /* Statistics of the last call on g (host struct). */
 rd_status rd_last_call_stats(const rd_graph* g, rd_call_stats* out);

@@ -35,6 +35,7 @@ RD_Q_PLAIN = 4
 RD_Q_PROFILE = 8
 RD_Q_NO_COMPACT = 16
 RD_Q_NO_ONCHIP = 32
+RD_Q_NO_TUNE = 64
 
 
 class QueryOpts(C.Structure):
@@ -64,6 +65,7 @@ class CallStats(C.Structure):
         ("ld", C.c_int64),
         ("spmm_bytes", C.c_double),
         ("compactions", C.c_int32),
+        ("tuned", C.c_int32),
     ]
 
 
@@ -80,6 +82,7 @@ EXPORTS = [
     "rd_power_method",
     "rd_triangle_weights",
     "rd_query_noalloc",
+    "rd_autotune",
     "rd_last_call_stats",
     "rd_status_string",
     "rd_last_error",
@@ -114,6 +117,8 @@ def declare(lib):
     lib.rd_triangle_weights.restype = C.c_int
     lib.rd_query_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, P, P, C.c_int64, C.POINTER(QueryOpts), P, P, P]
     lib.rd_query_noalloc.restype = C.c_int
+    lib.rd_autotune.argtypes = [P, C.c_int64, C.POINTER(QueryOpts), P, P, P, P]
+    lib.rd_autotune.restype = C.c_int
     lib.rd_last_call_stats.argtypes = [P, C.POINTER(CallStats)]
     lib.rd_last_call_stats.restype = C.c_int
     lib.rd_status_string.argtypes = [C.c_int]

@@ -47,12 +47,15 @@ int spmm_blocks_per_sm(const SpmmCfg& c, bool weighted, bool heavy, bool fp64)
 
 std::vector<SpmmCfg> spmm_configs(bool fp64) { return fp64 ? spmm_configs_f64() : spmm_configs_f32(); }
 
-static bool cfg_known(const SpmmCfg& c, bool fp64)
+static bool cfg_listed(const SpmmCfg& c, bool fp64)
 {
     for (const auto& x : spmm_configs(fp64))
         if (x == c) return true;
     return false;
 }
+
+// A step configuration is usable when it and its heavy-row pre-pass are instantiated.
+static bool cfg_known(const SpmmCfg& c, bool fp64) { return cfg_listed(c, fp64) && cfg_listed(heavy_cfg(c), fp64); }
 
 // ------------------------------------------------------------- helpers
 static bool is_device_ptr(const void* p)
@@ -300,6 +303,7 @@ static rd_status graph_build(rd_graph* g, const int64_t* row_ptr, const int32_t*
 // ------------------------------------------------------------- planning
 struct Plan {
     bool fp64;
+    bool tuned = false;     // cfg taken from the autotuner's table
     SpmmCfg cfg;
     int64_t ld;
     int grid_main, grid_heavy, grid_norm, nslab;
@@ -307,9 +311,44 @@ struct Plan {
     size_t elem;
 };
 
-static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bool fp64, bool plain)
+// ------------------------------------------------------------- autotuner keys
+// The tuner times the candidate SpMM configurations of a query width on the graph itself
+// and keeps the fastest per (precision, single-column or batched, width class); widths are
+// classed by the smallest power-of-two tile that holds them.
+static bool tuning_allowed(const rd_query_opts& o)
+{
+    return o.kernel == 0 && o.rhs_tile <= 0 && o.rows_per_warp <= 0 && (o.flags & RD_Q_NO_TUNE) == 0;
+}
+
+static int64_t tune_width(int64_t P, bool fp64, bool single)
+{
+    if (single) return 1;
+    const int64_t tmin = fp64 ? 8 : 16, tmax = fp64 ? 128 : 256;
+    int64_t w = tmin;
+    while (w < P && w < tmax) w <<= 1;
+    return w;
+}
+
+static const rd_graph::TunedCfg* find_tuned(const rd_graph* g, bool fp64, bool single, int64_t width)
+{
+    for (const auto& t : g->tuned)
+        if (t.fp64 == (int)fp64 && t.single == (int)single && t.width == width) return &t;
+    return nullptr;
+}
+
+static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bool fp64, bool plain,
+                        bool* from_table = nullptr)
 {
     const double mdeg = g->n ? (double)g->nnz / (double)g->n : 0.0;
+    if (from_table) *from_table = false;
+    if (tuning_allowed(o)) {
+        const bool single = plain || P == 1;
+        const rd_graph::TunedCfg* t = find_tuned(g, fp64, single, tune_width(P, fp64, single));
+        if (t) {
+            if (from_table) *from_table = true;
+            return t->cfg;
+        }
+    }
     SpmmCfg c;
     if (plain || P == 1) {
         c.vec = 1;
@@ -341,11 +380,11 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     return c;
 }
 
-static rd_status make_plan(rd_graph* g, int64_t P, const rd_query_opts& o, bool plain, Plan* pl)
+static rd_status make_plan_cfg(rd_graph* g, int64_t P, const rd_query_opts& o, const SpmmCfg& cfg, Plan* pl)
 {
     pl->fp64 = o.mode == RD_MODE_FP64;
     pl->elem = pl->fp64 ? 8 : 4;
-    pl->cfg = pick_cfg(g, P, o, pl->fp64, plain);
+    pl->cfg = cfg;
     if (!cfg_known(pl->cfg, pl->fp64)) {
         set_error("no SpMM kernel for rhs_tile/rows_per_warp = " + std::to_string(pl->cfg.tp()) + "/" +
                   std::to_string(pl->cfg.rpw()));
@@ -370,10 +409,20 @@ static rd_status make_plan(rd_graph* g, int64_t P, const rd_query_opts& o, bool 
     int bph = spmm_blocks_per_sm(pl->cfg, g->weighted, true, pl->fp64);
     if (bph < 1) bph = 1;
     int64_t gh = (int64_t)bph * g->sm_count;
-    gh = std::min<int64_t>(gh, (g->n_chunks + rows_per_block - 1) / rows_per_block);
+    const int chunks_per_block = kWarps * heavy_cfg(pl->cfg).rpw();
+    gh = std::min<int64_t>(gh, (g->n_chunks + chunks_per_block - 1) / chunks_per_block);
     pl->grid_heavy = (int)std::max<int64_t>(gh, 1);
     const int64_t vunits = (g->n * pl->ld) / (16 / (int64_t)pl->elem) + 1;
     pl->grid_norm = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 8, (vunits + 255) / 256));
+    return RD_OK;
+}
+
+static rd_status make_plan(rd_graph* g, int64_t P, const rd_query_opts& o, bool plain, Plan* pl)
+{
+    bool from_table = false;
+    const SpmmCfg cfg = pick_cfg(g, P, o, o.mode == RD_MODE_FP64, plain, &from_table);
+    RD_TRY(make_plan_cfg(g, P, o, cfg, pl));
+    pl->tuned = from_table;
     return RD_OK;
 }
 
@@ -849,6 +898,7 @@ static void record_stats(RunCtx& c)
     s.ld = c.pl.ld;
     s.spmm_bytes += c.spmm_bytes;
     s.compactions += c.compactions;
+    s.tuned = c.pl.tuned ? 1 : 0;
     if (c.profile) {
         double ms = 0.0;
         for (auto& pr : c.spmm_ev) {
@@ -902,6 +952,112 @@ static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t
     return RD_OK;
 }
 
+// ------------------------------------------------------------- autotuner
+// Candidates for one width class: for each tile from a quarter of the width up to the
+// width, the row-stream kernel and the row-group kernel with 1, 2 or 4 nonzero lanes per
+// row group; for one column, the warp-per-task SpMV, the row-stream kernel with one lane
+// per task and the row-group kernel with 4 to 32 nonzero lanes per row.
+static std::vector<SpmmCfg> tune_candidates(const rd_graph* g, int64_t width, bool fp64, bool single)
+{
+    std::vector<SpmmCfg> v;
+    auto add = [&](int vec, int gs, int nzl, int kind) {
+        SpmmCfg c;
+        c.vec = vec;
+        c.gs = gs;
+        c.nzl = nzl;
+        c.kind = kind;
+        if (cfg_known(c, fp64)) v.push_back(c);
+    };
+    if (single) {
+        if (g->ntasks > 0) add(1, 1, 1, 2);
+        add(1, 1, 1, 1);
+        for (int z : {4, 8, 16, 32}) add(1, 1, z, 0);
+        return v;
+    }
+    const int64_t tmin = fp64 ? 8 : 16;
+    for (int64_t tp = std::max(tmin, width / 4); tp <= width; tp <<= 1) {
+        const int vec = fp64 ? (tp >= 128 ? 4 : 2) : (tp >= 256 ? 8 : 4);
+        const int gs = (int)(tp / vec);
+        add(vec, gs, 1, 1);
+        for (int z : {1, 2, 4})
+            if (gs * z <= 32) add(vec, gs, z, 0);
+    }
+    return v;
+}
+
+// Mean time of one SpMM step launch pair (heavy-row pre-pass + main kernel) of cfg on g's
+// CSR with `width` columns: zeroed vectors, one warm-up and three timed launches.
+template <typename T>
+static rd_status time_cfg(rd_graph* g, int64_t width, const rd_query_opts& o, const SpmmCfg& cfg, cudaStream_t st,
+                          EventPool& ev, float* us_out)
+{
+    RunCtx c;
+    c.g = g;
+    c.o = o;
+    c.st = st;
+    c.P = width;
+    c.ev = &ev;
+    RD_TRY(make_plan_cfg(g, width, o, cfg, &c.pl));
+    c.cur = c.pl;
+    Carver dry(nullptr);
+    const size_t bytes = carve(dry, g, c.pl, width, false, &c.b, false);
+    RD_TRY(ensure_ws(g, bytes));
+    Carver real(g->ws.base);
+    carve(real, g, c.pl, width, false, &c.b, false);
+    RD_CUDA(cudaMemsetAsync(c.b.region_a, 0, 2 * block_bytes(g->n, c.pl.ld, c.pl.elem), st));
+    RD_CUDA(cudaMemsetAsync(static_cast<char*>(g->ws.base) + c.b.state_bytes_begin, 0,
+                            c.b.state_bytes_end - c.b.state_bytes_begin, st));
+    RD_CUDA(cudaMemsetAsync(c.b.st.act_count, 0x01, sizeof(int32_t), st));  // step 0 "active"
+    RD_TRY(enqueue_spmm<T>(c, 0, true));
+    cudaEvent_t e0 = ev.get(), e1 = ev.get();
+    RD_CUDA(cudaEventRecord(e0, st));
+    constexpr int kReps = 3;
+    for (int r = 0; r < kReps; ++r) RD_TRY(enqueue_spmm<T>(c, 0, true));
+    RD_CUDA(cudaEventRecord(e1, st));
+    RD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    *us_out = 1e3f * ms / kReps;
+    return RD_OK;
+}
+
+// Tune the width classes a query of P pairs can use (all of them down to the narrowest
+// tile when the query compacts), skipping classes already in g's table.
+static rd_status ensure_tuned(rd_graph* g, int64_t P, const rd_query_opts& o, bool plain, bool compact,
+                              cudaStream_t st)
+{
+    if (!tuning_allowed(o) || P < 1 || g->n == 0) return RD_OK;
+    const bool fp64 = o.mode == RD_MODE_FP64;
+    const bool single = plain || P == 1;
+    std::vector<int64_t> widths{tune_width(P, fp64, single)};
+    const int64_t tmin = fp64 ? 8 : 16;
+    if (compact && !single)
+        for (int64_t w = widths[0] / 2; w >= tmin; w /= 2) widths.push_back(w);
+    EventPool ev;
+    for (int64_t w : widths) {
+        if (find_tuned(g, fp64, single, w)) continue;
+        rd_graph::TunedCfg best;
+        best.us = -1.f;
+        for (const SpmmCfg& cfg : tune_candidates(g, w, fp64, single)) {
+            float us = 0.f;
+            rd_status r = fp64 ? time_cfg<double>(g, w, o, cfg, st, ev, &us)
+                               : time_cfg<float>(g, w, o, cfg, st, ev, &us);
+            if (r == RD_ERR_OOM) continue;  // a wider padding that does not fit is not a candidate
+            if (r < 0) return r;
+            if (best.us < 0.f || us < best.us) {
+                best.cfg = cfg;
+                best.us = us;
+            }
+        }
+        if (best.us < 0.f) continue;  // nothing fitted: the fixed rule decides
+        best.fp64 = fp64 ? 1 : 0;
+        best.single = single ? 1 : 0;
+        best.width = w;
+        g->tuned.push_back(best);
+    }
+    return RD_OK;
+}
+
 static rd_status prepare_run(RunCtx& c, rd_graph* g, int64_t P, const rd_query_opts& o, bool plain, bool grad,
                              cudaStream_t st, bool compact = false, bool lagged_polls = false)
 {
@@ -912,6 +1068,7 @@ static rd_status prepare_run(RunCtx& c, rd_graph* g, int64_t P, const rd_query_o
     c.profile = (o.flags & RD_Q_PROFILE) != 0;
     c.compact = compact;
     c.lagged_polls = lagged_polls && c.ev != nullptr;
+    RD_TRY(ensure_tuned(g, P, o, plain, compact, st));
     RD_TRY(make_plan(g, P, o, plain, &c.pl));
     c.cur = c.pl;
     Carver dry(nullptr);
@@ -1160,6 +1317,32 @@ rd_status rd_query(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npai
     RD_TRY(query_batch(g, s, t, npairs, o, false, r_out, iters_out, err_est_out, pair_status_out, st, &call, &ev,
                        compact, true));
     return call;
+}
+
+rd_status rd_autotune(rd_graph* g, int64_t npairs, const rd_query_opts* opts, int32_t* rhs_tile_out,
+                      int32_t* rows_per_warp_out, int32_t* kernel_out, void* stream)
+{
+    g_last_error.clear();
+    rd_query_opts o;
+    RD_TRY(validate_common(g, nullptr, nullptr, 0, opts, &o));
+    if (npairs < 1 || npairs > (1ll << 24)) {
+        set_error("npairs must be in [1, 2^24]");
+        return RD_ERR_INVALID_ARG;
+    }
+    if (!tuning_allowed(o)) {
+        set_error("rd_autotune needs rhs_tile, rows_per_warp and kernel at 0 and RD_Q_NO_TUNE unset");
+        return RD_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool plain = (o.flags & RD_Q_PLAIN) != 0;
+    RD_TRY(ensure_tuned(g, npairs, o, plain, !plain && (o.flags & RD_Q_NO_COMPACT) == 0, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    Plan pl;
+    RD_TRY(make_plan(g, plain ? 1 : npairs, o, plain, &pl));
+    if (rhs_tile_out) *rhs_tile_out = pl.cfg.tp();
+    if (rows_per_warp_out) *rows_per_warp_out = pl.cfg.rpw();
+    if (kernel_out) *kernel_out = pl.cfg.kind == 2 ? 3 : (pl.cfg.kind == 1 ? 2 : 1);
+    return RD_OK;
 }
 
 rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npairs, const double* grad_r,

@@ -45,6 +45,19 @@ struct SpmmCfg {
     }
 };
 
+// Configuration of the heavy-row pre-pass that goes with a step configuration: the same
+// column tile, one whole warp per chunk of a heavy row (GS column lanes x 32/GS nonzero
+// lanes), so that a chunk's gathers are spread over the warp instead of one row group.
+inline SpmmCfg heavy_cfg(const SpmmCfg& c)
+{
+    SpmmCfg h;
+    h.vec = c.vec;
+    h.gs = c.gs;
+    h.nzl = 32 / c.gs;
+    h.kind = 0;
+    return h;
+}
+
 constexpr int kBlock = 256;        // threads per block of the SpMM kernels
 constexpr int kWarps = kBlock / 32;
 constexpr int kRing = 4;           // increments kept for the delayed error estimate
@@ -219,6 +232,14 @@ struct rd_graph {
     rd_call_stats stats{};
     int* h_pinned = nullptr;          // small pinned host buffer for polls
     int64_t l2_bytes = 0;             // device L2 size
+    // SpMM configurations chosen by the autotuner on this graph, per width class
+    struct TunedCfg {
+        int fp64 = 0, single = 0;     // precision; single-column SpMV (plain / one pair) or batched
+        int64_t width = 0;            // width class (power-of-two tile holding the pairs; 1 if single)
+        rd::SpmmCfg cfg;
+        float us = 0.f;               // measured time of one SpMM launch pair
+    };
+    std::vector<TunedCfg> tuned;
 };
 
 namespace rd {

@@ -16,6 +16,9 @@ namespace rd {
     X(1, 1, 8)            \
     X(1, 1, 16)           \
     X(1, 1, 32)           \
+    X(2, 4, 8)            \
+    X(2, 8, 4)            \
+    X(2, 16, 2)           \
     X(2, 4, 1)            \
     X(2, 8, 1)            \
     X(2, 16, 1)           \
@@ -33,9 +36,9 @@ bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
 #undef X
         return false;
     }
-    // the heavy-row pre-pass of a row-stream config runs the row-group heavy kernel with the
-    // same column tile; single-column tiles use 8 nonzero lanes there
-    const int zl = (c.kind >= 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
+    // the heavy-row pre-pass runs the row-group heavy kernel with the same column tile and
+    // one warp per chunk (heavy_cfg)
+    const int zl = heavy ? heavy_cfg(c).nzl : c.nzl;
 #define X(V, G, Z) \
     if (c.vec == V && c.gs == G && zl == Z) return launch_cfg<double, V, G, Z>(weighted, heavy, grid, st, a);
     RD_F64_CONFIGS(X)
@@ -53,7 +56,7 @@ int spmm_blocks_per_sm_f64(const SpmmCfg& c, bool weighted, bool heavy)
 #undef X
         return 0;
     }
-    const int zl = (c.kind >= 1 && c.vec == 1 && c.gs == 1) ? 8 : c.nzl;
+    const int zl = heavy ? heavy_cfg(c).nzl : c.nzl;
 #define X(V, G, Z) \
     if (c.vec == V && c.gs == G && zl == Z) return occupancy_cfg<double, V, G, Z>(weighted, heavy);
     RD_F64_CONFIGS(X)

@@ -152,38 +152,73 @@ __device__ __forceinline__ bool pair_update(const FinArgs& a, const PairState& s
     return false;
 }
 
+// Columns per finalize block: 32, or the next power of two >= ld for narrower tiles, so
+// that the remaining threads of the block split the sum over the SpMM blocks.
+__host__ __device__ inline int fin_cols_per_block(int64_t ld)
+{
+    int cb = 1;
+    while (cb < ld && cb < 32) cb <<= 1;
+    return cb;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
 {
-    __shared__ double part[3][8][32];
-    const int lane = threadIdx.x & 31, split = threadIdx.x >> 5;
-    const int64_t col = (int64_t)blockIdx.x * 32 + lane;
+    __shared__ double part[3][256];
+    const int cb = fin_cols_per_block(a.ld);
+    const int nsplit = 256 / cb;
+    const int lane = threadIdx.x & (cb - 1), split = threadIdx.x / cb;
+    const int64_t col = (int64_t)blockIdx.x * cb + lane;
     const PairState& st = a.st;
     if (st.act_count[a.step] == 0) return;
+    // block partials b = split, split + nsplit, ...: four rows of loads in flight, summed
+    // in block order (the order depends only on nblocks and ld, so runs are repeatable)
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     if (col < a.ld) {
         const int64_t slab = col / a.tp, cin = col % a.tp;
-        for (int b = split; b < a.nblocks; b += 8) {
-            const double* bp = a.block_part + ((slab * a.nblocks + b) * 3) * a.tp + cin;
+        const double* base = a.block_part + slab * a.nblocks * 3 * a.tp + cin;
+        const int64_t bstride = 3 * (int64_t)a.tp;
+        int b = split;
+        for (; b + 3 * nsplit < a.nblocks; b += 4 * nsplit) {
+            double x[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double* bp = base + (int64_t)(b + u * nsplit) * bstride;
+                x[u][0] = bp[0];
+                x[u][1] = bp[a.tp];
+                x[u][2] = bp[2 * a.tp];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s0 += x[u][0];
+                s1 += x[u][1];
+                s2 += x[u][2];
+            }
+        }
+        for (; b < a.nblocks; b += nsplit) {
+            const double* bp = base + (int64_t)b * bstride;
             s0 += bp[0];
             s1 += bp[a.tp];
             s2 += bp[2 * a.tp];
         }
     }
-    part[0][split][lane] = s0;
-    part[1][split][lane] = s1;
-    part[2][split][lane] = s2;
+    part[0][threadIdx.x] = s0;
+    part[1][threadIdx.x] = s1;
+    part[2][threadIdx.x] = s2;
     __syncthreads();
+    // fixed-order tree over the splits
+    for (int h = nsplit >> 1; h >= 1; h >>= 1) {
+        if (split < h) {
+            part[0][threadIdx.x] += part[0][threadIdx.x + h * cb];
+            part[1][threadIdx.x] += part[1][threadIdx.x + h * cb];
+            part[2][threadIdx.x] += part[2][threadIdx.x + h * cb];
+        }
+        __syncthreads();
+    }
     if (split != 0 || col >= a.ld) return;
     const int p = a.slot_pair ? a.slot_pair[col] : (col < a.npairs ? (int)col : -1);
     if (p < 0 || !st.active[p]) return;
-    double A = 0.0, B = 0.0, C = 0.0;
-#pragma unroll
-    for (int sp = 0; sp < 8; ++sp) {
-        A += part[0][sp][lane];
-        B += part[1][sp][lane];
-        C += part[2][sp][lane];
-    }
+    const double A = part[0][lane], B = part[1][lane], C = part[2][lane];
     const int j = a.step;       // 0-based step index; Lanczos step i = j + 1
     const int64_t ld = a.ld;
     T* cfs = static_cast<T*>(a.cf_step);
@@ -207,7 +242,8 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
 
 void launch_finalize(cudaStream_t st, const FinArgs& a)
 {
-    const int nb = (int)((a.ld + 31) / 32);
+    const int cb = fin_cols_per_block(a.ld);
+    const int nb = (int)((a.ld + cb - 1) / cb);
     if (a.elem_size == 8) k_finalize<double><<<nb, 256, 0, st>>>(a);
     else k_finalize<float><<<nb, 256, 0, st>>>(a);
 }

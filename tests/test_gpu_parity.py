@@ -187,8 +187,9 @@ def test_scaling_by_four_is_bitwise(rd):
     G1 = rd.Graph.from_csr(g)
     G4 = rd.Graph(g.row_ptr, g.col, (4.0 * g.w).astype(np.float32))
     for mode in ["fp64", "fp32"]:
-        r1 = G1.query(s, t, mode=mode, k_max=40, fixed_k=True).r
-        r4 = G4.query(s, t, mode=mode, k_max=40, fixed_k=True).r
+        # the same kernel configuration on both graphs (the autotuner could time them apart)
+        r1 = G1.query(s, t, mode=mode, k_max=40, fixed_k=True, tune=False).r
+        r4 = G4.query(s, t, mode=mode, k_max=40, fixed_k=True, tune=False).r
         assert np.array_equal(r4 * 4.0, r1)
 
 
@@ -410,11 +411,59 @@ def test_workspace_allocation_failure_is_reported(rd):
     usable (allocation failure is the one device fault the library injects on purpose)."""
     g = F.path(200000)
     G = rd.Graph.from_csr(g)
+    s1, t1 = np.array([0, 5], np.int32), np.array([7, 99], np.int32)
+    before = G.query(s1, t1, mode="fp64", k_max=50, fixed_k=True).r
     big = 1 << 22                      # 4M pairs x 200k rows x 2 blocks x 4 bytes: ~6.4 TB
     s = np.zeros(big, np.int32)
     t = np.ones(big, np.int32)
     with pytest.raises(rd.RDError) as e:
         G.query(s, t, mode="fp32", k_max=4)
     assert e.value.status == rd.RD_ERR_OOM
-    ok = G.query(np.array([0], np.int32), np.array([7], np.int32), mode="fp64", rel_tol=0.0, resid_tol=1e-12)
-    assert ok.r[0] == pytest.approx(7.0, rel=1e-9)
+    after = G.query(s1, t1, mode="fp64", k_max=50, fixed_k=True).r
+    assert np.array_equal(before, after)
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_autotuner_choice_is_used_and_correct(rd, mode, tol):
+    """rd_autotune times the candidates on this graph and keeps the fastest; later queries use
+    it (stats say so), agree with the oracle, and with the fixed-rule configuration."""
+    g, s, t = W.chunglu(30000, 2.1, 20.0, 300000, 48, 91)
+    G = rd.Graph.from_csr(g)
+    ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=200, stop_tol=1e-14, threads=0)
+    pick = G.autotune(len(s), mode=mode)
+    assert pick["kernel"] in (1, 2) and pick["rhs_tile"] >= 8
+    res = G.query(s, t, mode=mode, k_max=200, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-7,
+                  compact=False)
+    st = G.last_stats()
+    assert st["tuned"] == 1 and st["rhs_tile"] == pick["rhs_tile"] and st["kernel"] == pick["kernel"]
+    assert rel(res.r, ref).max() < tol
+    fixed = G.query(s, t, mode=mode, k_max=200, rel_tol=0.0, resid_tol=1e-12 if mode == "fp64" else 1e-7,
+                    compact=False, tune=False)
+    assert G.last_stats()["tuned"] == 0
+    assert rel(fixed.r, ref).max() < tol
+    # the single-column path is tuned separately
+    one = G.autotune(1, mode=mode, plain=True)
+    assert one["rhs_tile"] == 1 and one["kernel"] in (1, 2, 3)
+    p = G.query(s[:3], t[:3], mode=mode, plain=True, k_max=200, rel_tol=0.0,
+                resid_tol=1e-12 if mode == "fp64" else 1e-7)
+    assert G.last_stats()["kernel"] == one["kernel"]
+    assert rel(p.r, ref[:3]).max() < tol
+
+
+def test_autotuner_first_use_and_arguments(rd):
+    """A query with default options tunes its width classes on first use (compacting query:
+    down to the narrowest tile); explicit tiles bypass the table; bad calls are rejected."""
+    g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 100, 5)
+    G = rd.Graph.from_csr(g)
+    a = G.query(s, t, k_max=200, rel_tol=1e-6)
+    assert G.last_stats()["tuned"] == 1
+    b = G.query(s, t, k_max=200, rel_tol=1e-6)
+    assert np.array_equal(a.r, b.r)              # same table entry, same summation order
+    G.query(s, t, k_max=200, rel_tol=1e-6, rhs_tile=32)
+    assert G.last_stats()["tuned"] == 0 and G.last_stats()["rhs_tile"] == 32
+    with pytest.raises(rd.RDError) as e:
+        G.autotune(16, rhs_tile=16)
+    assert e.value.status == rd.RD_ERR_INVALID_ARG
+    with pytest.raises(rd.RDError) as e:
+        G.autotune(0)
+    assert e.value.status == rd.RD_ERR_INVALID_ARG
