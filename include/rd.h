@@ -83,6 +83,9 @@ typedef enum {
 #define RD_Q_NO_TUNE 64u    /* with rhs_tile, rows_per_warp and kernel all 0: pick the SpMM
                                configuration by a fixed rule instead of the autotuner (see
                                rd_autotune) */
+#define RD_Q_NO_GRAPH 128u  /* rd_query: launch every kernel of every step from the host instead
+                               of replaying a captured CUDA graph of two steps (the results are
+                               bitwise the same; RD_Q_PROFILE also turns the graphs off) */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */

@@ -36,6 +36,7 @@ RD_Q_PROFILE = 8
 RD_Q_NO_COMPACT = 16
 RD_Q_NO_ONCHIP = 32
 RD_Q_NO_TUNE = 64
+RD_Q_NO_GRAPH = 128
 
 
 class QueryOpts(C.Structure):

@@ -112,6 +112,8 @@ static void free_graph(rd_graph* g)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
+    for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
+    if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
     delete g;
 }
 
@@ -446,6 +448,7 @@ struct Buffers {
     int32_t* status;
     int32_t* summary;
     int32_t* err_flag;
+    int32_t* step_dev;        // step index of graph-replayed steps (zeroed per query)
     // gradient / potential
     void* phi;
     void* coef_hist;
@@ -500,6 +503,7 @@ static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, boo
     s.act_count = c.take<int32_t>(K + 2);
     b->summary = c.take<int32_t>(2);
     b->err_flag = c.take<int32_t>(1);
+    b->step_dev = c.take<int32_t>(1);
     c.off = (c.off + 255) & ~size_t(255);
     b->state_bytes_end = c.off;
     b->s = c.take<int32_t>(P);
@@ -559,6 +563,7 @@ struct RunCtx {
     bool in_region_x = false;
     bool lazy_walk = false;  // Power Method steps instead of Lanczos steps
     bool onchip = false;     // whole recurrence per pair in one CTA (small graphs, queries only)
+    bool graph = false;      // steps replayed from a captured CUDA graph of two steps
     int compactions = 0;
     EventPool* ev = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
@@ -747,6 +752,118 @@ static rd_status enqueue_compaction(RunCtx& c, int active_upper)
     return RD_OK;
 }
 
+// ------------------------------------------------------------- CUDA graphs
+// One Lanczos step -- heavy-row pre-pass and SpMM, finalize, normalize, step advance -- is
+// captured once per argument set and replayed. Its kernels read the step index from
+// device memory (StepArgs::step_dev) and advance it themselves, so one graph per vector
+// block orientation serves every step of a query (the host swaps the two blocks' roles
+// after each step, as in the launch-per-kernel loop) and later queries with the same
+// layout. Polls, compaction and the stop test are the same as in that loop.
+constexpr size_t kGraphCache = 16;
+
+template <typename T>
+static void graph_step_args(RunCtx& c, const FinArgs& base, StepArgs<T>* sa, FinArgs* fa, NormArgs<T>* na)
+{
+    const int64_t ld = c.cur.ld;
+    const int64_t stride = c.compact ? 0 : 4 * ld;
+    T* cf0 = const_cast<T*>(coef_block<T>(c, 0));
+    memset(sa, 0, sizeof(*sa));
+    *sa = step_args<T>(c, 0, true);
+    sa->cf_beta = cf0;
+    sa->active_prev = nullptr;
+    sa->step_dev = c.b.step_dev;
+    sa->cf_stride = stride;
+    sa->act_count = c.b.st.act_count;
+    memset(fa, 0, sizeof(*fa));
+    *fa = base;
+    fa->step = 0;
+    fa->ld = ld;
+    fa->tp = c.cur.cfg.tp();
+    fa->nblocks = c.cur.grid_main;
+    fa->slot_pair = c.compact && c.slot_sel >= 0 ? c.b.slot_pair[c.slot_sel] : nullptr;
+    fa->cf_step = cf0;
+    fa->cf_next = c.compact ? cf0 : cf0 + 4 * ld;
+    fa->step_dev = c.b.step_dev;
+    fa->cf_stride = stride;
+    memset(na, 0, sizeof(*na));
+    na->n = c.g->n;
+    na->ld = ld;
+    na->w_to_qnext = static_cast<T*>(c.b.q[0]);
+    na->qcur = static_cast<const T*>(c.b.q[1]);
+    na->cf = cf0;
+    na->step_dev = c.b.step_dev;
+    na->cf_stride = stride;
+    na->act_count = c.b.st.act_count;
+}
+
+// Launch one step from the graph cache (capturing and instantiating it on a miss).
+template <typename T>
+static rd_status launch_step_graph(RunCtx& c, const FinArgs& base)
+{
+    rd_graph* g = c.g;
+    StepArgs<T> sa;
+    FinArgs fa;
+    NormArgs<T> na;
+    graph_step_args<T>(c, base, &sa, &fa, &na);
+    const bool heavy = g->n_chunks > 0;
+    int misc[8] = {c.cur.cfg.vec, c.cur.cfg.gs, c.cur.cfg.nzl, c.cur.cfg.kind, c.cur.grid_main, c.cur.grid_heavy,
+                   c.cur.grid_norm, c.pl.k_max};
+    std::string key(reinterpret_cast<const char*>(misc), sizeof(misc));
+    key.append(reinterpret_cast<const char*>(&sa), sizeof(sa));
+    key.append(reinterpret_cast<const char*>(&fa), sizeof(fa));
+    key.append(reinterpret_cast<const char*>(&na), sizeof(na));
+    key.push_back(sizeof(T) == 8 ? 'd' : 'f');
+    cudaGraphExec_t exec = nullptr;
+    for (const auto& kv : g->graphs)
+        if (kv.first == key) {
+            exec = kv.second;
+            break;
+        }
+    if (!exec) {
+        if (!g->capture_stream) RD_CUDA(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = g->capture_stream;
+        RD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        bool ok = true;
+        if (heavy)
+            ok = sizeof(T) == 8 ? launch_spmm_f64(c.cur.cfg, g->weighted, true, c.cur.grid_heavy, cs,
+                                                  *reinterpret_cast<const StepArgs<double>*>(&sa))
+                                : launch_spmm_f32(c.cur.cfg, g->weighted, true, c.cur.grid_heavy, cs,
+                                                  *reinterpret_cast<const StepArgs<float>*>(&sa));
+        if (ok)
+            ok = sizeof(T) == 8 ? launch_spmm_f64(c.cur.cfg, g->weighted, false, c.cur.grid_main, cs,
+                                                  *reinterpret_cast<const StepArgs<double>*>(&sa))
+                                : launch_spmm_f32(c.cur.cfg, g->weighted, false, c.cur.grid_main, cs,
+                                                  *reinterpret_cast<const StepArgs<float>*>(&sa));
+        if (ok) {
+            launch_finalize(cs, fa);
+            if constexpr (sizeof(T) == 8) launch_normalize_f64(c.cur.grid_norm, cs, na);
+            else launch_normalize_f32(c.cur.grid_norm, cs, na);
+            launch_step_advance(cs, c.b.step_dev, c.pl.k_max);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+        if (!ok) {
+            if (graph) cudaGraphDestroy(graph);
+            set_error("no SpMM kernel for this configuration");
+            return RD_ERR_UNSUPPORTED;
+        }
+        RD_CUDA(ec);
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        RD_CUDA(ei);
+        if (g->graphs.size() >= kGraphCache) {
+            cudaGraphExecDestroy(g->graphs.front().second);
+            g->graphs.erase(g->graphs.begin());
+        }
+        g->graphs.emplace_back(std::move(key), exec);
+    }
+    RD_CUDA(cudaGraphLaunch(exec, c.st));
+    c.launches += (heavy ? 2 : 1) + 3;
+    ++c.spmm_launches;
+    c.spmm_bytes += spmm_launch_bytes(g, c.cur);
+    return RD_OK;
+}
+
 template <typename T>
 static rd_status run_forward(RunCtx& c)
 {
@@ -801,29 +918,34 @@ static rd_status run_forward(RunCtx& c)
             return RD_OK;
         }
     }
+    c.graph = !c.profile && (c.o.flags & RD_Q_NO_GRAPH) == 0;
     constexpr int kSlots = 4;   // pinned poll slots h[4 .. 7]
     cudaEvent_t poll_ev[kSlots] = {};
     if (c.lagged_polls)
         for (int i = 0; i < kSlots; ++i) poll_ev[i] = c.ev->get();
     int last_known = h[1];
     for (int j = 0; j < c.pl.k_max; ++j) {
-        RD_TRY(enqueue_spmm<T>(c, j, true));
-        fa.step = j;
-        fa.ld = c.cur.ld;
-        fa.tp = c.cur.cfg.tp();
-        fa.nblocks = c.cur.grid_main;
-        if (c.compact) {
-            fa.slot_pair = c.slot_sel >= 0 ? c.b.slot_pair[c.slot_sel] : nullptr;
-            fa.cf_step = c.b.cf_cur[c.cf_sel];
-            fa.cf_next = c.b.cf_cur[c.cf_sel];
+        if (c.graph) {
+            RD_TRY(launch_step_graph<T>(c, fa));
         } else {
-            fa.slot_pair = nullptr;
-            fa.cf_step = static_cast<T*>(c.b.cf_hist) + (int64_t)j * 4 * c.cur.ld;
-            fa.cf_next = static_cast<T*>(c.b.cf_hist) + (int64_t)(j + 1) * 4 * c.cur.ld;
+            RD_TRY(enqueue_spmm<T>(c, j, true));
+            fa.step = j;
+            fa.ld = c.cur.ld;
+            fa.tp = c.cur.cfg.tp();
+            fa.nblocks = c.cur.grid_main;
+            if (c.compact) {
+                fa.slot_pair = c.slot_sel >= 0 ? c.b.slot_pair[c.slot_sel] : nullptr;
+                fa.cf_step = c.b.cf_cur[c.cf_sel];
+                fa.cf_next = c.b.cf_cur[c.cf_sel];
+            } else {
+                fa.slot_pair = nullptr;
+                fa.cf_step = static_cast<T*>(c.b.cf_hist) + (int64_t)j * 4 * c.cur.ld;
+                fa.cf_next = static_cast<T*>(c.b.cf_hist) + (int64_t)(j + 1) * 4 * c.cur.ld;
+            }
+            launch_finalize(c.st, fa);
+            ++c.launches;
+            enqueue_normalize<T>(c, j, false);
         }
-        launch_finalize(c.st, fa);
-        ++c.launches;
-        enqueue_normalize<T>(c, j, false);
         std::swap(c.b.q[0], c.b.q[1]);
         c.steps = j + 1;
         if (j + 1 >= c.pl.k_max) break;
@@ -1740,6 +1862,8 @@ extern "C" rd_status rd_query_noalloc(int64_t n, int64_t nnz, const int64_t* row
     rd_query_opts o;
     RD_TRY(validate_common(&g, s, t, npairs, opts, &o));
     o.flags &= ~RD_Q_PROFILE;  // no event objects
+    // no timing runs (they could need a larger workspace) and no graph objects
+    o.flags |= RD_Q_NO_TUNE | RD_Q_NO_GRAPH;
     o.kernel = 1;              // row-group kernel: needs no task list
     if (npairs == 0) return RD_OK;
 

@@ -89,7 +89,27 @@ struct StepArgs {
     const int32_t* active_prev;    // early exit when *active_prev == 0 (nullable)
     int do_reduce;
     int lazy_walk;                 // Power Method step: W = (1/2) q + (1/2) D^{-1} W_adj q (no recurrence)
+    // Step index read from device memory (graph replay; nullable): then the step j's
+    // beta_i row is cf_beta + j * cf_stride and the early-exit count is act_count[j].
+    const int32_t* step_dev;
+    int64_t cf_stride;
+    const int32_t* act_count;
 };
+
+// Step-dependent operands of a StepArgs launch (fixed pointers, or derived from the step
+// index in device memory when the launch is replayed from a CUDA graph).
+template <typename T>
+__device__ __forceinline__ const T* step_cf_beta(const StepArgs<T>& a)
+{
+    return a.step_dev ? a.cf_beta + (int64_t)(*a.step_dev) * a.cf_stride : a.cf_beta;
+}
+
+template <typename T>
+__device__ __forceinline__ bool step_inactive(const StepArgs<T>& a)
+{
+    const int32_t* p = a.step_dev ? a.act_count + *a.step_dev : a.active_prev;
+    return p != nullptr && *p == 0;
+}
 
 template <typename T>
 struct NormArgs {
@@ -100,6 +120,9 @@ struct NormArgs {
     T* phi;                        // nullable: phi += coef * q_i (replay pass)
     const T* coef;                 // ld, with phi
     const int32_t* active_prev;
+    const int32_t* step_dev;       // as StepArgs: cf + j * cf_stride, act_count[j]
+    int64_t cf_stride;
+    const int32_t* act_count;
 };
 
 // Per-pair FP64 state of the running LDL^T factorisation of I - T_k.
@@ -133,6 +156,8 @@ struct FinArgs {
     void* cf_step;                      // T [4][ld]: rows 1..3 receive alpha_i, c_i, 1/beta_{i+1}
     void* cf_next;                      // T [4][ld]: row 0 receives beta_{i+1} for the next step
     int elem_size;
+    const int32_t* step_dev;            // nullable: step index from device memory (graph replay);
+    int64_t cf_stride;                  // then cf_step/cf_next advance by j * cf_stride
 };
 
 // Whole recurrence of one pair per CTA with q_{i-1}, q_i and W in shared memory (graphs
@@ -240,6 +265,10 @@ struct rd_graph {
         float us = 0.f;               // measured time of one SpMM launch pair
     };
     std::vector<TunedCfg> tuned;
+    // instantiated CUDA graphs of two Lanczos steps, keyed by the bytes of their launch
+    // arguments (oldest evicted first), and the stream they are captured on
+    std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace rd {
@@ -256,6 +285,8 @@ std::vector<SpmmCfg> spmm_configs(bool fp64);
 void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a);
 void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a);
 void launch_finalize(cudaStream_t st, const FinArgs& a);
+// Advance the device step index by one, saturating at `limit` (end of a replayed step).
+void launch_step_advance(cudaStream_t st, int32_t* step, int limit);
 
 struct InitArgs {
     int64_t n, ld;

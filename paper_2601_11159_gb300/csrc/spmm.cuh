@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm_heavy(const StepArgs<T> a)
 {
     constexpr int TP = VEC * GS;
     constexpr int RPW = 32 / (GS * NZL);
-    if (a.active_prev && *a.active_prev == 0) return;
+    if (step_inactive(a)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cl = lane % GS, zl = (lane / GS) % NZL;
     const int rs = lane / (GS * NZL);
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(const StepArgs<T> a)
     constexpr int TP = VEC * GS;
     constexpr int RPW = 32 / (GS * NZL);
     __shared__ double red[kWarps][TP];
-    if (a.active_prev && *a.active_prev == 0) return;
+    if (step_inactive(a)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cl = lane % GS, zl = (lane / GS) % NZL;
     const int rs = lane / (GS * NZL);
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(const StepArgs<T> a)
     for (int slab = 0; slab < nslab; ++slab) {
         const int64_t c0 = (int64_t)slab * TP + cl * VEC;
         T bt[VEC];
-        ld_plain<T, VEC>(bt, a.cf_beta + c0);
+        ld_plain<T, VEC>(bt, step_cf_beta(a) + c0);
         Acc<T> sA[VEC], sB[VEC], sC[VEC];
 
         for (int64_t row = slot0; row < a.n; row += nslots) {
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
     constexpr int NH = CH / GS;          // indices held per lane
     extern __shared__ __align__(16) float smem_f[];
     double(*red)[TP] = reinterpret_cast<double(*)[TP]>(smem_f + SmemAcc<T, VEC>::kWords * kBlock);
-    if (a.active_prev && *a.active_prev == 0) return;
+    if (step_inactive(a)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = lane % GS, grp = lane / GS;
     const unsigned mask = group_mask<GS, 1>(lane);
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
     for (int slab = 0; slab < nslab; ++slab) {
         const int64_t c0 = (int64_t)slab * TP + gl * VEC;
         T bt[VEC];
-        ld_plain<T, VEC>(bt, a.cf_beta + c0);
+        ld_plain<T, VEC>(bt, step_cf_beta(a) + c0);
         SmemAcc<T, VEC> sacc;
         sacc.init(smem_f);
         RowBatch<T, VEC> rb;
@@ -782,11 +782,11 @@ __global__ void __launch_bounds__(kBlock) k_spmv_tasks(const StepArgs<T> a)
 {
     __shared__ T prod[kWarps][kTaskNnz];
     __shared__ double red[kWarps][1];
-    if (a.active_prev && *a.active_prev == 0) return;
+    if (step_inactive(a)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = gridDim.x * kWarps;
     const int ntasks = (int)a.ntasks;
-    const T bt = a.cf_beta[0];
+    const T bt = step_cf_beta(a)[0];
     Acc<T> sA, sB, sC;
     T* pw = prod[warp];
     for (int task = blockIdx.x * kWarps + warp; task < ntasks; task += nwarps) {
@@ -872,8 +872,10 @@ int occupancy_spmv_tasks(bool weighted)
     return nb;
 }
 
+// Dynamic shared-memory limit of the row-stream kernels, set once per instantiation (from
+// the occupancy query of planning, i.e. before any launch or stream capture uses it).
 template <typename T, int VEC, int GS>
-bool launch_rows_cfg(bool weighted, int grid, cudaStream_t st, const StepArgs<T>& a)
+void rows_smem_attr()
 {
     constexpr size_t sm = rows_smem_bytes<T, VEC, VEC * GS>();
     static bool attr = false;
@@ -882,6 +884,13 @@ bool launch_rows_cfg(bool weighted, int grid, cudaStream_t st, const StepArgs<T>
         cudaFuncSetAttribute(k_spmm_rows<T, VEC, GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
+}
+
+template <typename T, int VEC, int GS>
+bool launch_rows_cfg(bool weighted, int grid, cudaStream_t st, const StepArgs<T>& a)
+{
+    constexpr size_t sm = rows_smem_bytes<T, VEC, VEC * GS>();
+    rows_smem_attr<T, VEC, GS>();
     if (weighted) k_spmm_rows<T, VEC, GS, true><<<grid, kBlock, sm, st>>>(a);
     else k_spmm_rows<T, VEC, GS, false><<<grid, kBlock, sm, st>>>(a);
     return true;
@@ -892,8 +901,7 @@ int occupancy_rows_cfg(bool weighted)
 {
     int nb = 0;
     constexpr size_t sm = rows_smem_bytes<T, VEC, VEC * GS>();
-    cudaFuncSetAttribute(k_spmm_rows<T, VEC, GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_spmm_rows<T, VEC, GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    rows_smem_attr<T, VEC, GS>();
     if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_rows<T, VEC, GS, true>, kBlock, sm);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_rows<T, VEC, GS, false>, kBlock, sm);
     return nb;

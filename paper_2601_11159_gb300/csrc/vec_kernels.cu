@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
     const int lane = threadIdx.x & (cb - 1), split = threadIdx.x / cb;
     const int64_t col = (int64_t)blockIdx.x * cb + lane;
     const PairState& st = a.st;
-    if (st.act_count[a.step] == 0) return;
+    const int j = a.step_dev ? *a.step_dev : a.step;  // 0-based step index; Lanczos step i = j + 1
+    if (st.act_count[j] == 0) return;
     // block partials b = split, split + nsplit, ...: four rows of loads in flight, summed
     // in block order (the order depends only on nblocks and ld, so runs are repeatable)
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
@@ -219,10 +220,10 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
     const int p = a.slot_pair ? a.slot_pair[col] : (col < a.npairs ? (int)col : -1);
     if (p < 0 || !st.active[p]) return;
     const double A = part[0][lane], B = part[1][lane], C = part[2][lane];
-    const int j = a.step;       // 0-based step index; Lanczos step i = j + 1
     const int64_t ld = a.ld;
-    T* cfs = static_cast<T*>(a.cf_step);
-    T* cfn = static_cast<T*>(a.cf_next);
+    const int64_t cfo = a.step_dev ? (int64_t)j * a.cf_stride : 0;
+    T* cfs = static_cast<T*>(a.cf_step) + cfo;
+    T* cfn = static_cast<T*>(a.cf_next) + cfo;
     double alpha, cdef, beta_next;
     const bool stop = pair_update(a, st, p, j, A, B, C, &alpha, &cdef, &beta_next);
     if (stop) {
@@ -254,15 +255,17 @@ void launch_finalize(cudaStream_t st, const FinArgs& a)
 template <typename T, bool LD1>
 __global__ void __launch_bounds__(256) k_normalize(const NormArgs<T> a)
 {
-    if (a.active_prev && *a.active_prev == 0) return;
+    const int32_t* act = a.step_dev ? a.act_count + *a.step_dev : a.active_prev;
+    if (act && *act == 0) return;
+    const T* cfb = a.step_dev ? a.cf + (int64_t)(*a.step_dev) * a.cf_stride : a.cf;
     constexpr int V = 16 / (int)sizeof(T);
     const int64_t total = a.n * a.ld;
     const int64_t units = total / V;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t ld = a.ld;
-    const T* cf_al = a.cf + ld;
-    const T* cf_c = a.cf + 2 * ld;
-    const T* cf_ib = a.cf + 3 * ld;
+    const T* cf_al = cfb + ld;
+    const T* cf_c = cfb + 2 * ld;
+    const T* cf_ib = cfb + 3 * ld;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += stride) {
         const int64_t e0 = u * V;
         T w[V], qc[V], qn[V];
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(256) k_normalize(const NormArgs<T> a)
         const int64_t t0 = units * V;
         for (int64_t e = t0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
             const T w = a.w_to_qnext[e], qc = a.qcur[e];
-            a.w_to_qnext[e] = (w - a.cf[ld] * qc - a.cf[2 * ld]) * a.cf[3 * ld];
+            a.w_to_qnext[e] = (w - cf_al[0] * qc - cf_c[0]) * cf_ib[0];
             if (a.phi) a.phi[e] += a.coef[0] * qc;
         }
     }
@@ -316,6 +319,13 @@ static void launch_norm(int grid, cudaStream_t st, const NormArgs<T>& a)
     if (a.ld == 1) k_normalize<T, true><<<grid, 256, 0, st>>>(a);
     else k_normalize<T, false><<<grid, 256, 0, st>>>(a);
 }
+
+__global__ void k_step_advance(int32_t* step, int limit)
+{
+    if (*step < limit) *step += 1;
+}
+
+void launch_step_advance(cudaStream_t st, int32_t* step, int limit) { k_step_advance<<<1, 1, 0, st>>>(step, limit); }
 
 void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a) { launch_norm<float>(grid, st, a); }
 void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a) { launch_norm<double>(grid, st, a); }

@@ -467,3 +467,29 @@ def test_autotuner_first_use_and_arguments(rd):
     with pytest.raises(rd.RDError) as e:
         G.autotune(0)
     assert e.value.status == rd.RD_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_graph_replay_is_bitwise_the_launch_loop(rd, mode):
+    """Steps replayed from the captured two-step CUDA graph (step index in device memory)
+    give bitwise the results of launching every kernel from the host: compacting query with
+    the error-estimate stop, fixed k (odd, so the last graph half runs idle), the plain
+    path, and the gradient (whose replay pass must regenerate the forward vectors)."""
+    g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 70, 13)
+    G = rd.Graph.from_csr(g)
+    for kw in (dict(k_max=200, rel_tol=1e-7), dict(k_max=200, rel_tol=0.0, resid_tol=1e-9),
+               dict(k_max=7, fixed_k=True), dict(k_max=200, rel_tol=1e-7, compact=False)):
+        a = G.query(s, t, mode=mode, **kw)
+        ga = G.last_stats()
+        b = G.query(s, t, mode=mode, graph=False, **kw)
+        assert np.array_equal(a.r, b.r), kw
+        assert np.array_equal(a.iters, b.iters) and np.array_equal(a.status, b.status), kw
+        assert ga["compactions"] == G.last_stats()["compactions"] or not kw.get("compact", True)
+    pa = G.query(s[:5], t[:5], mode=mode, plain=True, k_max=200, rel_tol=1e-7)
+    pb = G.query(s[:5], t[:5], mode=mode, plain=True, k_max=200, rel_tol=1e-7, graph=False)
+    assert np.array_equal(pa.r, pb.r) and np.array_equal(pa.iters, pb.iters)
+    ga, ra = G.edge_grad(s[:16], t[:16], None, mode=mode, k_max=200, rel_tol=0.0, resid_tol=1e-9)
+    gb, rb = G.edge_grad(s[:16], t[:16], None, mode=mode, k_max=200, rel_tol=0.0, resid_tol=1e-9, graph=False)
+    assert np.array_equal(ra, rb) and np.array_equal(ga, gb)
+    ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=200, stop_tol=1e-14, threads=0)
+    assert rel(a.r, ref).max() < (FP64_TOL if mode == "fp64" else FP32_TOL)
