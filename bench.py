@@ -335,6 +335,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=256)
     ap.add_argument("--kernel", default="tuned", choices=["tuned", "group", "stream"])
     ap.add_argument("--rhs-tile", type=int, default=0)
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "roadgrid", "all"],
                     help="extra measurements instead of the main line")
     args = ap.parse_args()
@@ -379,6 +381,8 @@ def main():
     spmm_bytes = 0.0
     steps_max = 0
     compactions = 0
+    if args.profile_range:
+        torch.cuda.profiler.start()
     e0.record(stream)
     for _ in range(args.steps):
         res = G.query(s_dev, t_dev, profile=True, **opts)
@@ -391,6 +395,8 @@ def main():
         compactions += st["compactions"]
     e1.record(stream)
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     barrier(world)
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)

@@ -100,8 +100,10 @@ typedef struct {
                               rd_query polls every step, one step behind the device. */
     uint32_t flags;        /* RD_Q_* */
     int32_t kernel;        /* SpMM kernel: 0 = tuned, 1 = row-group (warp lanes split a row's
-                              nonzeros), 2 = row-stream (row groups walk runs of consecutive rows);
-                              with one pair the tuned choice is the warp-per-task SpMV */
+                              nonzeros), 2 = row-stream (row groups walk runs of consecutive rows),
+                              3 = row-group visiting the rows by decreasing degree (the row groups
+                              of a warp then hold rows of equal length); with one pair the fixed
+                              rule (RD_Q_NO_TUNE) takes the warp-per-task SpMV */
 } rd_query_opts;
 
 /* Per-call statistics of the last rd_query / rd_edge_grad / rd_potential on g. */
@@ -120,6 +122,7 @@ typedef struct {
                                 ld in force at that launch (it shrinks as converged pairs are packed) */
     int32_t compactions;     /* times the active pairs were packed into a narrower block */
     int32_t tuned;           /* 1 if the configuration came from the autotuner's table */
+    int32_t row_order;       /* 1 if the row-group kernel visited rows by decreasing degree */
 } rd_call_stats;
 
 /* Fill `opts` with defaults: k_max 1000, rel_tol 1e-7, resid_tol 0, FP32 vectors with FP64

@@ -67,6 +67,7 @@ class CallStats(C.Structure):
         ("spmm_bytes", C.c_double),
         ("compactions", C.c_int32),
         ("tuned", C.c_int32),
+        ("row_order", C.c_int32),
     ]
 
 

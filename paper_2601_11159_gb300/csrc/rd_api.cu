@@ -49,8 +49,9 @@ std::vector<SpmmCfg> spmm_configs(bool fp64) { return fp64 ? spmm_configs_f64() 
 
 static bool cfg_listed(const SpmmCfg& c, bool fp64)
 {
+    if (c.order && c.kind != 0) return false;  // the row order is a row-group kernel option
     for (const auto& x : spmm_configs(fp64))
-        if (x == c) return true;
+        if (x.vec == c.vec && x.gs == c.gs && x.nzl == c.nzl && x.kind == c.kind) return true;
     return false;
 }
 
@@ -108,7 +109,8 @@ static void free_graph(rd_graph* g)
 {
     if (!g) return;
     void* ptrs[] = {g->row_ptr, g->col, g->w, g->keep_idx, g->deg64, g->invdeg64, g->deg32, g->invdeg32,
-                    g->comp, g->heavy_rows, g->heavy_first, g->chunk_beg, g->chunk_end, g->task_row, g->ws.base};
+                    g->comp, g->heavy_rows, g->heavy_first, g->chunk_beg, g->chunk_end, g->task_row,
+                    g->row_order, g->ws.base};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
@@ -189,6 +191,18 @@ static rd_status build_heavy(rd_graph* g, const std::vector<int64_t>& rp)
     g->ntasks = (int64_t)tasks.size() - 1;
     RD_CUDA(cudaMalloc((void**)&g->task_row, sizeof(int32_t) * tasks.size()));
     RD_CUDA(cudaMemcpy(g->task_row, tasks.data(), sizeof(int32_t) * tasks.size(), cudaMemcpyHostToDevice));
+    // rows by decreasing degree, stable (counting sort on the degree)
+    {
+        int64_t dmax = 0;
+        for (int64_t u = 0; u < g->n; ++u) dmax = std::max<int64_t>(dmax, rp[u + 1] - rp[u]);
+        std::vector<int64_t> start((size_t)dmax + 2, 0);
+        for (int64_t u = 0; u < g->n; ++u) ++start[(size_t)(dmax - (rp[u + 1] - rp[u])) + 1];
+        for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+        std::vector<int32_t> order((size_t)std::max<int64_t>(g->n, 1));
+        for (int64_t u = 0; u < g->n; ++u) order[(size_t)start[(size_t)(dmax - (rp[u + 1] - rp[u]))]++] = (int32_t)u;
+        RD_CUDA(cudaMalloc((void**)&g->row_order, sizeof(int32_t) * order.size()));
+        RD_CUDA(cudaMemcpy(g->row_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice));
+    }
     if (g->n_heavy_rows == 0) return RD_OK;
     RD_CUDA(cudaMalloc((void**)&g->heavy_rows, sizeof(int32_t) * rows.size()));
     RD_CUDA(cudaMalloc((void**)&g->heavy_first, sizeof(int32_t) * first.size()));
@@ -367,6 +381,7 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
         }
         c.nzl = mdeg <= 6 ? 4 : (mdeg <= 12 ? 8 : (mdeg <= 24 ? 16 : 32));
         if (o.rows_per_warp > 0) c.nzl = std::max(1, std::min(32, 32 / o.rows_per_warp));
+        c.order = o.kernel == 3 && g->row_order ? 1 : 0;
         return c;
     }
     int tp = o.rhs_tile;
@@ -377,7 +392,8 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     c.vec = fp64 ? (tp >= 128 ? 4 : 2) : (tp >= 256 ? 8 : 4);
     c.gs = std::max(1, tp / c.vec);
     c.nzl = 1;
-    c.kind = o.kernel == 1 ? 0 : 1;  // row-stream unless the row-group kernel is asked for
+    c.kind = o.kernel == 1 || o.kernel == 3 ? 0 : 1;  // row-stream unless a row-group kernel is asked for
+    c.order = o.kernel == 3 && g->row_order ? 1 : 0;
     if (c.kind == 0 && o.rows_per_warp > 0) c.nzl = std::max(1, 32 / (c.gs * o.rows_per_warp));
     return c;
 }
@@ -613,6 +629,7 @@ static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
     a.heavy_part = static_cast<T*>(c.b.heavy_part);
     a.ntasks = g->ntasks;
     a.task_row = g->task_row;
+    a.row_order = c.cur.cfg.kind == 0 && c.cur.cfg.order ? g->row_order : nullptr;
     // rows whose current slab fits in half of L2 are gathered with L2 priority
     a.hot_rows = g->l2_bytes > 0 ? (int64_t)(g->l2_bytes / 2) / (c.cur.cfg.tp() * (int64_t)sizeof(T)) : 0;
     a.block_part = c.b.block_part;
@@ -1021,6 +1038,7 @@ static void record_stats(RunCtx& c)
     s.spmm_bytes += c.spmm_bytes;
     s.compactions += c.compactions;
     s.tuned = c.pl.tuned ? 1 : 0;
+    s.row_order = c.pl.cfg.order;
     if (c.profile) {
         double ms = 0.0;
         for (auto& pr : c.spmm_ev) {
@@ -1053,8 +1071,8 @@ static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t
         set_error("k_max must be in [1, 2^22]");
         return RD_ERR_INVALID_ARG;
     }
-    if (o->kernel < 0 || o->kernel > 2) {
-        set_error("kernel must be 0, 1 or 2");
+    if (o->kernel < 0 || o->kernel > 3) {
+        set_error("kernel must be 0, 1, 2 or 3");
         return RD_ERR_INVALID_ARG;
     }
     if (o->mode != RD_MODE_FP64 && o->mode != RD_MODE_FP32V_FP64S) {
@@ -1082,27 +1100,31 @@ static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t
 static std::vector<SpmmCfg> tune_candidates(const rd_graph* g, int64_t width, bool fp64, bool single)
 {
     std::vector<SpmmCfg> v;
-    auto add = [&](int vec, int gs, int nzl, int kind) {
+    auto add = [&](int vec, int gs, int nzl, int kind, int order) {
         SpmmCfg c;
         c.vec = vec;
         c.gs = gs;
         c.nzl = nzl;
         c.kind = kind;
+        c.order = order;
+        if (order && !g->row_order) return;
         if (cfg_known(c, fp64)) v.push_back(c);
     };
     if (single) {
-        if (g->ntasks > 0) add(1, 1, 1, 2);
-        add(1, 1, 1, 1);
-        for (int z : {4, 8, 16, 32}) add(1, 1, z, 0);
+        if (g->ntasks > 0) add(1, 1, 1, 2, 0);
+        add(1, 1, 1, 1, 0);
+        for (int z : {4, 8, 16, 32})
+            for (int o : {0, 1}) add(1, 1, z, 0, o);
         return v;
     }
     const int64_t tmin = fp64 ? 8 : 16;
     for (int64_t tp = std::max(tmin, width / 4); tp <= width; tp <<= 1) {
         const int vec = fp64 ? (tp >= 128 ? 4 : 2) : (tp >= 256 ? 8 : 4);
         const int gs = (int)(tp / vec);
-        add(vec, gs, 1, 1);
+        add(vec, gs, 1, 1, 0);
         for (int z : {1, 2, 4})
-            if (gs * z <= 32) add(vec, gs, z, 0);
+            if (gs * z <= 32)
+                for (int o : {0, 1}) add(vec, gs, z, 0, o);
     }
     return v;
 }

@@ -37,11 +37,12 @@ rd_status cuda_status(cudaError_t e, const char* what);
 // (k_spmm_rows, grid-stride over tasks of consecutive rows; nzl must be 1).
 struct SpmmCfg {
     int vec = 4, gs = 32, nzl = 1, kind = 0;
+    int order = 0;  // row-group kernel: 1 = visit rows by decreasing degree (rd_graph::row_order)
     int tp() const { return vec * gs; }
     int rpw() const { return 32 / (gs * nzl); }
     bool operator==(const SpmmCfg& o) const
     {
-        return vec == o.vec && gs == o.gs && nzl == o.nzl && kind == o.kind;
+        return vec == o.vec && gs == o.gs && nzl == o.nzl && kind == o.kind && order == o.order;
     }
 };
 
@@ -94,6 +95,9 @@ struct StepArgs {
     const int32_t* step_dev;
     int64_t cf_stride;
     const int32_t* act_count;
+    // row-group kernel: visiting order of the rows (nullable = 0 .. n-1); rows of equal
+    // degree are adjacent, so the row groups of a warp finish their rows together
+    const int32_t* row_order;
 };
 
 // Step-dependent operands of a StepArgs launch (fixed pointers, or derived from the step
@@ -252,6 +256,8 @@ struct rd_graph {
     int task_nnz = 512;
     int64_t ntasks = 0;
     int32_t* task_row = nullptr;
+    // rows by decreasing degree (stable: equal degrees in row order)
+    int32_t* row_order = nullptr;
     double mean_deg = 0.0;
     rd::Workspace ws;
     rd_call_stats stats{};

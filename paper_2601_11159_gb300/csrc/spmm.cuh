@@ -409,7 +409,8 @@ __global__ void __launch_bounds__(kBlock) k_spmm(const StepArgs<T> a)
         ld_plain<T, VEC>(bt, step_cf_beta(a) + c0);
         Acc<T> sA[VEC], sB[VEC], sC[VEC];
 
-        for (int64_t row = slot0; row < a.n; row += nslots) {
+        for (int64_t i = slot0; i < a.n; i += nslots) {
+            const int64_t row = a.row_order ? (int64_t)a.row_order[i] : i;
             const int64_t beg = a.row_ptr[row], end = a.row_ptr[row + 1];
             T acc[VEC], qp[VEC], qc[VEC];
 #pragma unroll

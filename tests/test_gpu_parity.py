@@ -51,7 +51,7 @@ SMALL = [
 
 @pytest.mark.parametrize("name,make", SMALL)
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
-@pytest.mark.parametrize("kernel", ["group", "stream", "onchip"])
+@pytest.mark.parametrize("kernel", ["group", "group_sorted", "stream", "onchip"])
 def test_small_graphs_vs_dense(rd, name, make, mode, kernel):
     g = make()
     s, t = F.random_pairs(g.n, 9, 17)
@@ -87,7 +87,7 @@ def test_grid64_corner_fp64_closed_form(rd):
     assert res.status[0] == 0 and res.iters[0] < 500
     assert rel(res.r, [ref]).max() < FP64_TOL
     # the same with the single-vector SpMV paths (row-group and row-stream kernels)
-    for kernel in ["group", "stream"]:
+    for kernel in ["group", "group_sorted", "stream"]:
         res1 = G.query(s, t, mode="fp64", k_max=500, rel_tol=0.0, resid_tol=1e-10, plain=True, kernel=kernel)
         assert rel(res1.r, [ref]).max() < FP64_TOL
 
@@ -161,7 +161,7 @@ def test_self_loops_dropped(rd):
 
 
 @pytest.mark.parametrize("mode,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
-@pytest.mark.parametrize("kernel", ["group", "stream"])
+@pytest.mark.parametrize("kernel", ["group", "group_sorted", "stream"])
 def test_batched_vs_plain_and_order(rd, mode, tol, kernel):
     g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 40, 77)
     G = rd.Graph.from_csr(g)
@@ -376,9 +376,9 @@ def test_plain_kernels_agree(rd):
     g, s, t = W.chunglu(30000, 2.1, 20.0, 300000, 6, 17)
     G = rd.Graph.from_csr(g)
     out = [G.query(s, t, mode=m, k_max=40, fixed_k=True, plain=True, kernel=k).r
-           for m in ["fp64"] for k in ["tuned", "group", "stream"]]
-    assert G.last_stats()["kernel"] == 2
-    assert rel(out[1], out[0]).max() < 1e-12 and rel(out[2], out[0]).max() < 1e-12
+           for m in ["fp64"] for k in ["tuned", "group", "stream", "group_sorted"]]
+    assert G.last_stats()["kernel"] == 1 and G.last_stats()["row_order"] == 1
+    assert max(rel(o, out[0]).max() for o in out[1:]) < 1e-12
     r32 = G.query(s, t, mode="fp32", k_max=40, fixed_k=True, plain=True).r
     assert rel(r32, out[0]).max() < 2e-5
 
