@@ -83,6 +83,9 @@ typedef enum {
 #define RD_Q_NO_TUNE 64u    /* with rhs_tile, rows_per_warp and kernel all 0: pick the SpMM
                                configuration by a fixed rule instead of the autotuner (see
                                rd_autotune) */
+#define RD_Q_EST_DELAYED 256u /* rel_tol test on the sum of the last 4 increments of
+                               e_1^T (I-T_k)^{-1} e_1 (the error of the estimate 4 steps back)
+                               instead of the default geometric tail estimate (see rel_tol) */
 #define RD_Q_NO_GRAPH 128u  /* rd_query: launch every kernel of every step from the host instead
                                of replaying a captured CUDA graph of two steps (the results are
                                bitwise the same; RD_Q_PROFILE also turns the graphs off) */
@@ -90,7 +93,11 @@ typedef enum {
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */
     double rel_tol;        /* stop when the estimated relative error of r is <= rel_tol (0 = off);
-                              estimate: the last 4 increments of e_1^T (I-T_k)^{-1} e_1 over its value */
+                              estimate (from step 4 on): with d_j the increments of
+                              S_k = e_1^T (I-T_k)^{-1} e_1 and rho the largest of the last three
+                              ratios d_j / d_{j-1} (at least 1/2), d_k * rho / (1 - rho)^2 / S_k,
+                              the tail of a geometric series with a margin for slow decay; not
+                              a bound (RD_Q_EST_DELAYED selects the delayed-sum estimate) */
     double resid_tol;      /* stop when ||b - (I - Ahat) x_k|| / ||b|| <= resid_tol (0 = off) */
     int32_t mode;          /* rd_mode */
     int32_t rhs_tile;      /* right-hand-side columns per SpMM sweep; 0 = tuned */

@@ -37,6 +37,7 @@ RD_Q_NO_COMPACT = 16
 RD_Q_NO_ONCHIP = 32
 RD_Q_NO_TUNE = 64
 RD_Q_NO_GRAPH = 128
+RD_Q_EST_DELAYED = 256
 
 
 class QueryOpts(C.Structure):

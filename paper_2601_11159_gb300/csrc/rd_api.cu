@@ -896,6 +896,7 @@ static rd_status run_forward(RunCtx& c)
     fa.fp64 = sizeof(T) == 8;
     fa.rel_tol = c.o.rel_tol;
     fa.resid_tol = c.o.resid_tol;
+    fa.est_delayed = (c.o.flags & RD_Q_EST_DELAYED) ? 1 : 0;
     fa.sumdeg = c.g->sumdeg;
     fa.block_part = c.b.block_part;
     fa.st = c.b.st;

@@ -153,6 +153,7 @@ struct FinArgs {
     int npairs, tp, nblocks, step;      // step: 0-based index of the step just reduced
     int k_max, deflate, fixed_k, fp64;
     double rel_tol, resid_tol, sumdeg;
+    int est_delayed;                    // 1: delayed-sum error estimate (RD_Q_EST_DELAYED)
     const double* block_part;
     PairState st;
     int64_t pstride;                    // stride of the per-pair [k][pair] arrays (original ld)

@@ -118,10 +118,24 @@ __device__ __forceinline__ bool pair_update(const FinArgs& a, const PairState& s
         beta_next = sqrt(fmax(beta2, 0.0));
         const double resid = beta_next * fabs(g / delta);
         st.resid[p] = resid;
+        // Relative error estimate of r_k = b2 * S_k: the increments still to come. Default:
+        // their sum as a series whose ratio is the largest of the last kRing-1 increment
+        // ratios (at least 1/2), with an extra margin 1/(1 - rho) for slowly converging
+        // pairs: incr * rho / (1 - rho)^2. Alternative (est_delayed): the sum of the last
+        // kRing increments, i.e. the error of the estimate kRing steps back.
         double tail = 0.0;
         const int nr = j + 1 < kRing ? j + 1 : kRing;
         for (int q = 0; q < nr; ++q) tail += st.ring[(int64_t)q * np + p];
-        const double est = tail / S;
+        double est = tail / S;
+        if (!a.est_delayed && j + 1 >= kRing) {
+            double rho = 0.5;
+            for (int q = 1; q < kRing; ++q) {
+                const double num = st.ring[(int64_t)((j - q + 1) % kRing) * np + p];
+                const double den = st.ring[(int64_t)((j - q) % kRing) * np + p];
+                rho = fmax(rho, num / den);
+            }
+            est = rho < 1.0 ? incr * rho / ((1.0 - rho) * (1.0 - rho)) / S : INFINITY;
+        }
         st.err[p] = est;
         st.hist_alpha[(int64_t)j * np + p] = alpha;
         st.hist_beta[(int64_t)(j + 1) * np + p] = beta_next;

@@ -492,4 +492,36 @@ def test_graph_replay_is_bitwise_the_launch_loop(rd, mode):
     gb, rb = G.edge_grad(s[:16], t[:16], None, mode=mode, k_max=200, rel_tol=0.0, resid_tol=1e-9, graph=False)
     assert np.array_equal(ra, rb) and np.array_equal(ga, gb)
     ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=200, stop_tol=1e-14, threads=0)
-    assert rel(a.r, ref).max() < (FP64_TOL if mode == "fp64" else FP32_TOL)
+    assert rel(a.r, ref).max() < 1e-7        # the last query's rel_tol
+
+
+@pytest.mark.parametrize("family", ["chunglu", "rmat", "ba", "grid_del", "grid"])
+def test_error_estimate_stop_meets_rel_tol(rd, family):
+    """The rel_tol stop (geometric tail estimate) returns estimates within rel_tol of the
+    converged value on the method's workload families, and on fast-mixing graphs stops no
+    later than the delayed-sum estimate."""
+    from graphgen.graph import largest_component
+
+    if family == "chunglu":
+        g, s, t = W.chunglu(30000, 2.1, 20.0, 300000, 32, 41)
+    elif family == "rmat":
+        g = largest_component(F.rmat(14, 16, 0.57, 0.19, 0.19, 8))
+        s, t = F.random_pairs(g.n, 32, 6)
+    elif family == "ba":
+        g = F.barabasi_albert(8000, 4, 6)
+        s, t = F.random_pairs(g.n, 32, 7)
+    elif family == "grid_del":
+        g = F.grid_deleted(40, 0.05, 11)
+        s, t = F.random_pairs(g.n, 16, 8)
+    else:
+        g = F.grid(48)
+        s, t = F.random_pairs(g.n, 16, 9)
+    ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=5000, stop_tol=1e-15, threads=0)
+    G = rd.Graph.from_csr(g)
+    for tol in (1e-4, 1e-6, 1e-8):
+        res = G.query(s, t, mode="fp64", k_max=5000, rel_tol=tol)
+        assert np.all(res.status == 0)
+        assert rel(res.r, ref).max() <= tol, (family, tol, rel(res.r, ref).max())
+        if family in ("chunglu", "rmat", "ba"):
+            old = G.query(s, t, mode="fp64", k_max=5000, rel_tol=tol, estimate="delayed")
+            assert np.all(res.iters <= old.iters)
