@@ -109,8 +109,9 @@ typedef struct {
     int32_t kernel;        /* SpMM kernel: 0 = tuned, 1 = row-group (warp lanes split a row's
                               nonzeros), 2 = row-stream (row groups walk runs of consecutive rows),
                               3 = row-group visiting the rows by decreasing degree (the row groups
-                              of a warp then hold rows of equal length); with one pair the fixed
-                              rule (RD_Q_NO_TUNE) takes the warp-per-task SpMV */
+                              of a warp then hold rows of equal length), 4 = warp-per-task SpMV
+                              (one column only: RD_Q_PLAIN or one pair; RD_ERR_UNSUPPORTED
+                              otherwise); with one column the fixed rule (RD_Q_NO_TUNE) takes 4 */
 } rd_query_opts;
 
 /* Per-call statistics of the last rd_query / rd_edge_grad / rd_potential on g. */
@@ -122,7 +123,7 @@ typedef struct {
     int32_t rhs_tile;        /* configuration used */
     int32_t rows_per_warp;
     int32_t nnz_lanes;       /* lanes that share one row's nonzeros */
-    int32_t kernel;          /* SpMM kernel used (1 = row-group, 2 = row-stream, 3 = single-column SpMV) */
+    int32_t kernel;          /* SpMM kernel used, numbered as rd_query_opts::kernel (1 .. 4) */
     int64_t ld;              /* padded number of right-hand-side columns (vector row stride) */
     double spmm_bytes;       /* algorithmic bytes of all SpMM launches of the call, each
                                 4*nnz (+4*nnz weights) + 8*(n+1) + 3*ld*n*sizeof(element) with the

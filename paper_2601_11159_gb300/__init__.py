@@ -118,7 +118,7 @@ def _opts(k_max=1000, rel_tol=1e-7, resid_tol=0.0, mode="fp32", rhs_tile=0, rows
     o.rhs_tile = int(rhs_tile)
     o.rows_per_warp = int(rows_per_warp)
     o.chunk_steps = int(chunk_steps)
-    o.kernel = ({"tuned": 0, "group": 1, "stream": 2, "group_sorted": 3}.get(kernel, kernel)
+    o.kernel = ({"tuned": 0, "group": 1, "stream": 2, "group_sorted": 3, "tasks": 4}.get(kernel, kernel)
                 if isinstance(kernel, str) else int(kernel))
     o.flags = ((RD_Q_FIXED_K if fixed_k else 0) | (0 if deflate else RD_Q_NO_DEFLATE) |
                (RD_Q_PLAIN if plain else 0) | (RD_Q_PROFILE if profile else 0) |

@@ -331,6 +331,14 @@ struct Plan {
 // The tuner times the candidate SpMM configurations of a query width on the graph itself
 // and keeps the fastest per (precision, single-column or batched, width class); widths are
 // classed by the smallest power-of-two tile that holds them.
+// rd_query_opts::kernel / rd_call_stats::kernel number of a configuration.
+static int kernel_code(const SpmmCfg& c)
+{
+    if (c.kind == 2) return 4;
+    if (c.kind == 1) return 2;
+    return c.order ? 3 : 1;
+}
+
 static bool tuning_allowed(const rd_query_opts& o)
 {
     return o.kernel == 0 && o.rhs_tile <= 0 && o.rows_per_warp <= 0 && (o.flags & RD_Q_NO_TUNE) == 0;
@@ -369,7 +377,7 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     if (plain || P == 1) {
         c.vec = 1;
         c.gs = 1;
-        if (o.kernel == 0 && g->ntasks > 0) {  // warp-per-task SpMV
+        if ((o.kernel == 0 || o.kernel == 4) && g->ntasks > 0) {  // warp-per-task SpMV
             c.nzl = 1;
             c.kind = 2;
             return c;
@@ -382,6 +390,11 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
         c.nzl = mdeg <= 6 ? 4 : (mdeg <= 12 ? 8 : (mdeg <= 24 ? 16 : 32));
         if (o.rows_per_warp > 0) c.nzl = std::max(1, std::min(32, 32 / o.rows_per_warp));
         c.order = o.kernel == 3 && g->row_order ? 1 : 0;
+        return c;
+    }
+    if (o.kernel == 4) {  // single-column only: no such tile (make_plan reports it)
+        c.kind = 2;
+        c.vec = 2;
         return c;
     }
     int tp = o.rhs_tile;
@@ -1034,7 +1047,7 @@ static void record_stats(RunCtx& c)
     s.rhs_tile = c.pl.cfg.tp();
     s.rows_per_warp = c.pl.cfg.rpw();
     s.nnz_lanes = c.pl.cfg.nzl;
-    s.kernel = c.pl.cfg.kind == 2 ? 3 : (c.pl.cfg.kind == 1 ? 2 : 1);
+    s.kernel = kernel_code(c.pl.cfg);
     s.ld = c.pl.ld;
     s.spmm_bytes += c.spmm_bytes;
     s.compactions += c.compactions;
@@ -1072,8 +1085,8 @@ static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t
         set_error("k_max must be in [1, 2^22]");
         return RD_ERR_INVALID_ARG;
     }
-    if (o->kernel < 0 || o->kernel > 3) {
-        set_error("kernel must be 0, 1, 2 or 3");
+    if (o->kernel < 0 || o->kernel > 4) {
+        set_error("kernel must be 0, 1, 2, 3 or 4");
         return RD_ERR_INVALID_ARG;
     }
     if (o->mode != RD_MODE_FP64 && o->mode != RD_MODE_FP32V_FP64S) {
@@ -1486,7 +1499,7 @@ rd_status rd_autotune(rd_graph* g, int64_t npairs, const rd_query_opts* opts, in
     RD_TRY(make_plan(g, plain ? 1 : npairs, o, plain, &pl));
     if (rhs_tile_out) *rhs_tile_out = pl.cfg.tp();
     if (rows_per_warp_out) *rows_per_warp_out = pl.cfg.rpw();
-    if (kernel_out) *kernel_out = pl.cfg.kind == 2 ? 3 : (pl.cfg.kind == 1 ? 2 : 1);
+    if (kernel_out) *kernel_out = kernel_code(pl.cfg);
     return RD_OK;
 }
 
