@@ -894,6 +894,11 @@ static rd_status launch_step_graph(RunCtx& c, const FinArgs& base)
     return RD_OK;
 }
 
+// Algorithmic bytes of one SpMM launch above which rd_query polls without lag (about a
+// quarter of a millisecond of HBM traffic on this part, against a host reaction of tens of
+// microseconds).
+constexpr double kNoLagBytes = 1.5e9;
+
 template <typename T>
 static rd_status run_forward(RunCtx& c)
 {
@@ -982,13 +987,17 @@ static rd_status run_forward(RunCtx& c)
         if (j + 1 >= c.pl.k_max) break;
         if (c.lagged_polls) {
             // count of active pairs after step j lands in h[4 + j % kSlots]; read the count
-            // of the previous step, whose copy has usually completed while step j runs
+            // of the previous step, whose copy has usually completed while step j runs --
+            // or, when a step is long enough (a step's SpMM moves more than kNoLagBytes),
+            // wait for step j's own count: the GPU idles for the host's reaction time, but
+            // converged pairs are packed out one step earlier
+            const int lag = spmm_launch_bytes(c.g, c.cur) > kNoLagBytes ? 0 : 1;
             const int sl = j % kSlots;
             RD_CUDA(cudaMemcpyAsync(h + 4 + sl, c.b.st.act_count + j + 1, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                     c.st));
             RD_CUDA(cudaEventRecord(poll_ev[sl], c.st));
-            if (j >= 1) {
-                const int ps = (j - 1) % kSlots;
+            if (j >= lag) {
+                const int ps = (j - lag) % kSlots;
                 RD_CUDA(cudaEventSynchronize(poll_ev[ps]));
                 last_known = h[4 + ps];
                 if (last_known == 0) break;  // steps enqueued since return at once
