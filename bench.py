@@ -211,6 +211,88 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_config_sweep(rd, timed):
+    """One JSON line per synthetic workload (sizes and recipes in graphgen/workloads.py):
+    grid64       -- one pair (corner to corner), FP64, plain single-vector path, stop at relative
+                    residual 1e-10; error against the dense pseudo-inverse;
+    chunglu1m    -- 256 pairs, FP32 vectors, rel_tol 1e-6: batched vs plain (16 pairs) pairs/s;
+                    error against the FP64 oracle on 32 sampled pairs;
+    roadgrid4096 -- 64 pairs, FP64, rel_tol 1e-6 (the FP32-vector floor at this condition number is
+                    about 5e-5, so FP32 runs to relative residual 1e-6 for time only); error of 4
+                    pairs against the same pairs run to relative residual 1e-10;
+    chunglu4m_w  -- 32 pairs, gradient over all edges (rd_edge_grad, FP32 vectors), gradients/s
+                    and the forward error against the oracle on 4 pairs;
+    rmat24       -- 128 pairs, FP32 vectors, rel_tol 1e-6: batched vs plain (8 pairs) pairs/s;
+                    error against the oracle on 8 sampled pairs."""
+    import torch
+
+    from graphgen import workloads as W
+    from oracle import dense
+    from oracle import lanczos as O
+
+    def line(**kw):
+        print(json.dumps(dict(sweep="configs", **kw)), flush=True)
+
+    def rel(a, b):
+        return float(np.max(np.abs(np.asarray(a, np.float64) / np.asarray(b, np.float64) - 1)))
+
+    g, s, t = W.grid64()
+    G = rd.Graph.from_csr(g)
+    exact = dense.DenseRD.of(g).r(s, t)
+    ms, res = timed(lambda: G.query(s, t, mode="fp64", k_max=500, rel_tol=0.0, resid_tol=1e-10, plain=True))
+    line(workload="grid64", pairs=1, mode="fp64", path="plain", query_ms=ms, pairs_per_s=1e3 / ms,
+         iters=int(res.iters[0]), max_rel_err=rel(res.r, exact))
+    G.close()
+
+    for name, make, pairs_plain in [("chunglu1m", W.chunglu1m, 16), ("rmat24", W.rmat24, 8)]:
+        g, s, t = make()
+        G = rd.Graph.from_csr(g)
+        sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
+        kw = dict(mode="fp32", k_max=200, rel_tol=1e-6)
+        ms_b, rb = timed(lambda: G.query(sd, td, **kw))
+        ms_p, rp = timed(lambda: G.query(sd[:pairs_plain], td[:pairs_plain], plain=True, **kw), reps=2)
+        idx = np.linspace(0, len(s) - 1, 32 if name == "chunglu1m" else 8).astype(int)
+        ref, _, _ = O.lanczos_batch(g, s[idx], t[idx], k_max=200, stop_tol=1e-13, threads=0)
+        rbn, rpn = rb.r.cpu().numpy(), rp.r.cpu().numpy()
+        pidx = idx[idx < pairs_plain]
+        line(workload=name, n=g.n, nnz=g.nnz, pairs=len(s), mode="fp32",
+             batched_pairs_per_s=len(s) / (ms_b / 1e3), plain_pairs_per_s=pairs_plain / (ms_p / 1e3),
+             batched_over_plain=(len(s) / ms_b) / (pairs_plain / ms_p),
+             iters_median=float(np.median(rb.iters.cpu().numpy())), iters_max=int(rb.iters.max()),
+             max_rel_err_batched=rel(rbn[idx], ref),
+             max_rel_err_plain=rel(rpn[pidx], ref[np.isin(idx, pidx)]) if len(pidx) else None,
+             sampled_pairs=len(idx))
+        G.close()
+
+    g, s, t = W.roadgrid4096()
+    G = rd.Graph.from_csr(g)
+    ms64, r64 = timed(lambda: G.query(s, t, mode="fp64", k_max=40000, rel_tol=1e-6), reps=1)
+    ms32, r32 = timed(lambda: G.query(s, t, mode="fp32", k_max=40000, rel_tol=0.0, resid_tol=1e-6), reps=1)
+    tight = G.query(s[:4], t[:4], mode="fp64", k_max=60000, rel_tol=0.0, resid_tol=1e-10)
+    line(workload="roadgrid4096", n=g.n, nnz=g.nnz, pairs=len(s),
+         fp64_rel_tol_1e6={"query_ms": ms64, "pairs_per_s": len(s) / (ms64 / 1e3),
+                           "iters_median": float(np.median(r64.iters)), "iters_max": int(r64.iters.max()),
+                           "max_rel_err_vs_resid1e-10": rel(r64.r[:4], tight.r)},
+         fp32_resid_1e6={"query_ms": ms32, "pairs_per_s": len(s) / (ms32 / 1e3),
+                         "iters_median": float(np.median(r32.iters)), "iters_max": int(r32.iters.max()),
+                         "max_rel_err_vs_resid1e-10": rel(r32.r[:4], tight.r)},
+         reference_iters=tight.iters.tolist())
+    G.close()
+
+    g, s, t = W.chunglu4m_w()
+    G = rd.Graph.from_csr(g)
+    ones = np.ones(len(s))
+    ms_g, (gw, r) = timed(lambda: G.edge_grad(s, t, ones, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
+    ms_f, rf = timed(lambda: G.query(s, t, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
+    idx = np.array([0, 9, 21, 30])
+    ref, _, _ = O.lanczos_batch(g, s[idx], t[idx], k_max=200, stop_tol=1e-13, threads=0)
+    line(workload="chunglu4m_w", n=g.n, nnz=g.nnz, pairs=len(s), mode="fp32",
+         gradient_ms=ms_g, gradients_per_s=len(s) / (ms_g / 1e3), forward_ms=ms_f,
+         gradient_over_forward=ms_g / ms_f, max_rel_err_r=rel(np.asarray(r)[idx], ref),
+         grad_entries=int(gw.size))
+    G.close()
+
+
 def run_sweeps(which: str):
     """Extra measurements beyond the main line (one JSON line each):
     scaling  -- Erdos-Renyi and Barabasi-Albert graphs, n = 1e2..1e6, m = n ln n, k = 20 fixed,
@@ -219,7 +301,10 @@ def run_sweeps(which: str):
                 random vertices (all ordered pairs), k = 15 / k = 5, absolute error against the
                 dense oracle (the s,t-selection and density experiment, Exp-6);
     pm       -- steps and time to relative error 1e-6 for the Lanczos iteration and the Power
-                Method (Algorithm 1) on a road-like grid and on a Chung-Lu graph."""
+                Method (Algorithm 1) on a road-like grid and on a Chung-Lu graph;
+    configs  -- the five synthetic workloads: pairs/s of the batched and the plain path at
+                relative error 1e-6 (gradients/s for the weighted Chung-Lu case), each with its
+                measured error (see run_config_sweep)."""
     import torch
 
     import paper_2601_11159_gb300 as rd
@@ -276,22 +361,8 @@ def run_sweeps(which: str):
                                       "mean_abs_err": float(np.mean(np.abs(r - exact))),
                                       "max_abs_err": float(np.max(np.abs(r - exact)))}), flush=True)
             G.close()
-    if which in ("roadgrid", "all"):
-        from graphgen import workloads as W
-
-        g, s, t = W.roadgrid4096()
-        G = rd.Graph.from_csr(g)
-        for mode, kw in [("fp64", dict(rel_tol=0.0, resid_tol=1e-8)), ("fp32", dict(rel_tol=0.0, resid_tol=1e-6))]:
-            ms, res = timed(lambda: G.query(s, t, mode=mode, k_max=40000, **kw), reps=1)
-            st = G.last_stats()
-            print(json.dumps({"sweep": "roadgrid4096", "mode": mode, "n": g.n, "nnz": g.nnz, "pairs": len(s),
-                              "query_ms": ms, "pairs_per_s": len(s) / (ms / 1000), "stop": kw,
-                              "iters_min": int(res.iters.min()), "iters_median": float(np.median(res.iters)),
-                              "iters_max": int(res.iters.max()), "status": np.unique(res.status).tolist(),
-                              "compactions": st["compactions"],
-                              "spmm_gbs_algorithmic": st["spmm_bytes"] / max(st["spmm_ms"], 1e-9) / 1e6,
-                              "r_sample": res.r[:4].tolist()}), flush=True)
-        G.close()
+    if which in ("configs", "all"):
+        run_config_sweep(rd, timed)
     if which in ("pm", "all"):
         from graphgen import workloads as W
 
@@ -337,7 +408,7 @@ def main():
     ap.add_argument("--rhs-tile", type=int, default=0)
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
-    ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "roadgrid", "all"],
+    ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "configs", "all"],
                     help="extra measurements instead of the main line")
     args = ap.parse_args()
     if args.sweep:
@@ -504,7 +575,10 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "k_spmm (+ k_spmm_heavy)", "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                      "algorithmic_bytes_per_launch": spmm_bytes / max(spmm_n, 1), "avg_launch_ms": avg_launch_ms,
-                     "launches_timed": spmm_n},
+                     "launches_timed": spmm_n,
+                     # DRAM bytes actually moved per launch (ncu, profiles/) over the live launch time
+                     "dram_gbs": traffic / (avg_launch_ms / 1e3) / 1e9 if traffic and avg_launch_ms else None,
+                     "dram_frac": traffic / (avg_launch_ms / 1e3) / 1e9 / peak if traffic and avg_launch_ms else None},
         "plain_pairs_per_s": plain_value,
         "batched_over_plain": None if plain_value is None else value / world / plain_value,
         "cpu_baseline": cpu,
