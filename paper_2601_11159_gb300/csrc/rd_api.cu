@@ -110,7 +110,7 @@ static void free_graph(rd_graph* g)
     if (!g) return;
     void* ptrs[] = {g->row_ptr, g->col, g->w, g->keep_idx, g->deg64, g->invdeg64, g->deg32, g->invdeg32,
                     g->comp, g->heavy_rows, g->heavy_first, g->chunk_beg, g->chunk_end, g->task_row,
-                    g->row_order, g->ws.base};
+                    g->row_order, g->entry_row, g->ws.base};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
@@ -1536,15 +1536,23 @@ rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t 
     rd_status call = RD_OK;
     RD_TRY(forward_and_potential(c, s, t, grad_r, &call));
     // edge kernel over internal entries, then map to the caller's entry order
-    const int grid = std::max(1, std::min(g->sm_count * 8, (int)((g->n + 7) / 8)));
+    if (!g->entry_row && g->nnz > 0) {
+        RD_CUDA(cudaMalloc((void**)&g->entry_row, sizeof(int32_t) * g->nnz));
+        launch_entry_rows(std::max(1, std::min(g->sm_count * 8, (int)((g->n + 7) / 8))), st, g->n, g->row_ptr,
+                          g->entry_row);
+        ++c.launches;
+    }
+    const int grid = std::max<int>(1, (int)std::min<int64_t>((int64_t)g->sm_count * 8, (g->nnz + 255) / 256));
     float* gint = c.b.grad;
     if (c.pl.fp64) {
         EdgeGradArgs<double> a{};
         a.n = g->n;
         a.ld = c.pl.ld;
+        a.nnz = g->nnz;
         a.npairs = (int)npairs;
         a.row_ptr = g->row_ptr;
         a.col = g->col;
+        a.entry_row = g->entry_row;
         a.phi = static_cast<const double*>(c.b.phi);
         a.gbar = static_cast<const double*>(c.b.gbar);
         a.grad_out = gint;
@@ -1553,9 +1561,11 @@ rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t 
         EdgeGradArgs<float> a{};
         a.n = g->n;
         a.ld = c.pl.ld;
+        a.nnz = g->nnz;
         a.npairs = (int)npairs;
         a.row_ptr = g->row_ptr;
         a.col = g->col;
+        a.entry_row = g->entry_row;
         a.phi = static_cast<const float*>(c.b.phi);
         a.gbar = static_cast<const float*>(c.b.gbar);
         a.grad_out = gint;

@@ -259,6 +259,8 @@ struct rd_graph {
     int32_t* task_row = nullptr;
     // rows by decreasing degree (stable: equal degrees in row order)
     int32_t* row_order = nullptr;
+    // row of every stored entry (built on first use by the per-entry kernels)
+    int32_t* entry_row = nullptr;
     double mean_deg = 0.0;
     rd::Workspace ws;
     rd_call_stats stats{};
@@ -336,16 +338,18 @@ void launch_zsolve(cudaStream_t st, const ZsolveArgs& a);
 
 template <typename T>
 struct EdgeGradArgs {
-    int64_t n, ld;
+    int64_t n, ld, nnz;
     int npairs;
     const int64_t* row_ptr;
     const int32_t* col;
+    const int32_t* entry_row;     // row of each stored entry (nnz)
     const T* phi;                 // n x ld
     const T* gbar;                // ld
     float* grad_out;              // internal entries
 };
 void launch_edge_grad_f32(int grid, cudaStream_t st, const EdgeGradArgs<float>& a);
 void launch_edge_grad_f64(int grid, cudaStream_t st, const EdgeGradArgs<double>& a);
+void launch_entry_rows(int grid, cudaStream_t st, int64_t n, const int64_t* row_ptr, int32_t* entry_row);
 
 // Graph preparation kernels.
 rd_status graph_prepare(rd_graph* g, cudaStream_t st, uint32_t flags);

@@ -420,38 +420,53 @@ void launch_zsolve(cudaStream_t st, const ZsolveArgs& a)
 
 // ---------------------------------------------------------- edge gradient
 // grad[e] = -1/2 sum_p gbar_p (phi_p(u) - phi_p(v))^2 for stored entry e = (u -> v).
-// A row group of GS lanes spans VEC*GS columns and loops over the column chunks.
+// Entries are processed in CSR order, kU consecutive entries per row group of GS lanes
+// (VEC*GS columns per column chunk), so the gathers of kU entries are in flight at once;
+// the row of each entry comes from the graph's entry-row array.
 template <typename T, int VEC, int GS>
 __global__ void __launch_bounds__(256) k_edge_grad(const EdgeGradArgs<T> a)
 {
     constexpr int TP = VEC * GS;
-    constexpr int RPW = 32 / GS;
+    constexpr int NG = 32 / GS;
+    constexpr int kU = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cl = lane % GS, rs = lane / GS;
+    const int cl = lane % GS, grp = lane / GS;
     const unsigned mask = group_mask<GS, 1>(lane);
-    const int64_t nslots = (int64_t)gridDim.x * (blockDim.x / 32) * RPW;
-    const int64_t slot0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + warp) * RPW + rs;
+    const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x / 32) * NG;
+    const int64_t gid = ((int64_t)blockIdx.x * (blockDim.x / 32) + warp) * NG + grp;
     const int nch = (int)(a.ld / TP);
-    for (int64_t row = slot0; row < a.n; row += nslots) {
-        const int64_t beg = a.row_ptr[row], end = a.row_ptr[row + 1];
-        for (int64_t e = beg; e < end; ++e) {
-            const int64_t v = __ldg(a.col + e);
-            float s = 0.f;
-            for (int ch = 0; ch < nch; ++ch) {
-                const int64_t c0 = (int64_t)ch * TP + cl * VEC;
-                T pu[VEC], pv[VEC], gb[VEC];
-                ld_gather<T, VEC>(pu, a.phi + row * a.ld + c0);
-                ld_gather<T, VEC>(pv, a.phi + v * a.ld + c0);
-                ld_gather<T, VEC>(gb, a.gbar + c0);
+    for (int64_t e0 = gid * kU; e0 < a.nnz; e0 += ngroups * kU) {
+        int64_t u[kU], v[kU];
+        float s[kU];
 #pragma unroll
-                for (int i = 0; i < VEC; ++i) {
-                    const T d = pu[i] - pv[i];
-                    s += (float)(gb[i] * d * d);
-                }
+        for (int k = 0; k < kU; ++k) {
+            const bool ok = e0 + k < a.nnz;
+            u[k] = ok ? (int64_t)__ldg(a.entry_row + e0 + k) : 0;
+            v[k] = ok ? (int64_t)__ldg(a.col + e0 + k) : 0;
+            s[k] = 0.f;
+        }
+        for (int ch = 0; ch < nch; ++ch) {
+            const int64_t c0 = (int64_t)ch * TP + cl * VEC;
+            T gb[VEC], pu[kU][VEC], pv[kU][VEC];
+            ld_gather<T, VEC>(gb, a.gbar + c0);
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                ld_gather<T, VEC>(pu[k], a.phi + u[k] * a.ld + c0);
+                ld_gather<T, VEC>(pv[k], a.phi + v[k] * a.ld + c0);
             }
 #pragma unroll
-            for (int off = 1; off < GS; off <<= 1) s += __shfl_xor_sync(mask, s, off);
-            if (cl == 0) a.grad_out[e] = -0.5f * s;
+            for (int k = 0; k < kU; ++k)
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    const T d = pu[k][i] - pv[k][i];
+                    s[k] += (float)(gb[i] * d * d);
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+#pragma unroll
+            for (int off = 1; off < GS; off <<= 1) s[k] += __shfl_xor_sync(mask, s[k], off);
+            if (cl == 0 && e0 + k < a.nnz) a.grad_out[e0 + k] = -0.5f * s[k];
         }
     }
 }
@@ -467,6 +482,20 @@ static void launch_eg(int grid, cudaStream_t st, const EdgeGradArgs<T>& a)
     else if (units % 4 == 0) k_edge_grad<T, VEC, 4><<<grid, 256, 0, st>>>(a);
     else if (units % 2 == 0) k_edge_grad<T, VEC, 2><<<grid, 256, 0, st>>>(a);
     else k_edge_grad<T, VEC, 1><<<grid, 256, 0, st>>>(a);
+}
+
+// Row of every stored entry (one warp per row, lanes strided over the row's entries).
+__global__ void __launch_bounds__(256) k_entry_rows(int64_t n, const int64_t* row_ptr, int32_t* entry_row)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); r < n; r += nw)
+        for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) entry_row[e] = (int32_t)r;
+}
+
+void launch_entry_rows(int grid, cudaStream_t st, int64_t n, const int64_t* row_ptr, int32_t* entry_row)
+{
+    k_entry_rows<<<grid, 256, 0, st>>>(n, row_ptr, entry_row);
 }
 
 void launch_edge_grad_f32(int grid, cudaStream_t st, const EdgeGradArgs<float>& a) { launch_eg<float>(grid, st, a); }
