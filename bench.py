@@ -52,14 +52,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def load_traffic():
+def load_traffic(workload: str):
     """DRAM bytes per SpMM launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    current kernel source and on this workload (else None)."""
     p = os.path.join(ROOT, "profiles", "spmm_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_source_sha1") != kernel_source_hash():
+    if d.get("kernel_source_sha1") != kernel_source_hash() or d.get("workload") != workload:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -536,7 +536,8 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
     # SpMM launches shrink as converged pairs are packed: total algorithmic bytes over total time
     avg_launch_ms = spmm_ms / max(spmm_n, 1)
     achieved = spmm_bytes / (spmm_ms / 1000.0) / 1e9 if spmm_n and spmm_ms > 0 else None
-    traffic = load_traffic()
+    workload_name = "chunglu1m_256pairs" if args.n == 1_000_000 and P == 256 else f"chunglu{args.n}_{P}pairs"
+    traffic = load_traffic(workload_name)
 
     cpu = None
     max_rel = None
@@ -557,8 +558,7 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "chunglu1m_256pairs" if args.n == 1_000_000 and P == 256 else
-                   f"chunglu{args.n}_{P}pairs", "n": g.n, "nnz": g.nnz, "pairs": P, "kernel": int(st["kernel"]),
+        "config": {"workload": workload_name, "n": g.n, "nnz": g.nnz, "pairs": P, "kernel": int(st["kernel"]),
                    "precision": "FP32 vectors and SpMM, FP64 alpha/beta/T_k and reductions",
                    "stop": f"estimated relative error <= {REL_TOL}", "k_max": K_MAX,
                    "lanczos_steps_max": int(steps_max), "iters_median": float(np.median(iters)),
