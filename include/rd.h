@@ -61,8 +61,13 @@ typedef enum {
 
 typedef enum {
     RD_MODE_FP64 = 0,        /* vectors, SpMV/SpMM and all scalars in FP64 */
-    RD_MODE_FP32V_FP64S = 1  /* vectors and SpMM in FP32; alpha, beta, T_k, its solve and every
+    RD_MODE_FP32V_FP64S = 1, /* vectors and SpMM in FP32; alpha, beta, T_k, its solve and every
                                 cross-thread reduction in FP64 */
+    RD_MODE_DF64 = 2         /* rd_query only (the other calls run it as RD_MODE_FP64): vectors
+                                stored as pairs of FP32 numbers (hi + lo, about 48 significant
+                                bits) with the element arithmetic on the FP32 units by error-free
+                                transformations; scalars as in RD_MODE_FP64. FP64-class accuracy
+                                where FP64 arithmetic, not memory, bounds the step */
 } rd_mode;
 
 /* rd_graph_create / rd_graph_set_weights flags */

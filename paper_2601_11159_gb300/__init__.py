@@ -23,7 +23,7 @@ from . import _lib
 from ._lib import (  # noqa: F401
     RD_OK, RD_WARN_NOT_CONVERGED, RD_ERR_INVALID_ARG, RD_ERR_ZERO_DEGREE, RD_ERR_DISCONNECTED,
     RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_TIMEOUT, RD_ERR_NUMERIC, RD_ERR_UNSUPPORTED,
-    RD_MODE_FP64, RD_MODE_FP32V_FP64S, RD_INPUT_ON_DEVICE, RD_CHECK_SYMMETRY, RD_LABEL_COMPONENTS,
+    RD_MODE_FP64, RD_MODE_FP32V_FP64S, RD_MODE_DF64, RD_INPUT_ON_DEVICE, RD_CHECK_SYMMETRY, RD_LABEL_COMPONENTS,
     RD_Q_FIXED_K, RD_Q_NO_DEFLATE, RD_Q_PLAIN, RD_Q_PROFILE, RD_Q_NO_COMPACT, RD_Q_NO_ONCHIP, RD_Q_NO_TUNE,
     RD_Q_NO_GRAPH, RD_Q_EST_DELAYED,
 )
@@ -113,6 +113,8 @@ def _opts(k_max=1000, rel_tol=1e-7, resid_tol=0.0, mode="fp32", rhs_tile=0, rows
         o.mode = RD_MODE_FP64
     elif mode in ("fp32", RD_MODE_FP32V_FP64S):
         o.mode = RD_MODE_FP32V_FP64S
+    elif mode in ("df64", RD_MODE_DF64):
+        o.mode = RD_MODE_DF64
     else:
         raise ValueError(f"unknown mode {mode!r}")
     o.rhs_tile = int(rhs_tile)

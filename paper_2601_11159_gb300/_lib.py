@@ -23,6 +23,7 @@ RD_ERR_NUMERIC = -7
 RD_ERR_UNSUPPORTED = -8
 
 RD_MODE_FP64 = 0
+RD_MODE_DF64 = 2
 RD_MODE_FP32V_FP64S = 1
 
 RD_INPUT_ON_DEVICE = 1

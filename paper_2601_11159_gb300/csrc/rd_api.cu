@@ -16,6 +16,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "rd_internal.cuh"
@@ -37,13 +38,19 @@ rd_status check_csr(rd_graph* g, cudaStream_t st, int64_t* self_loops);
 rd_status compute_degrees(rd_graph* g, cudaStream_t st);
 int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy);
 int spmm_blocks_per_sm_f64(const SpmmCfg& c, bool weighted, bool heavy);
+int spmm_blocks_per_sm_df64(const SpmmCfg& c, bool weighted, bool heavy);
 std::vector<SpmmCfg> spmm_configs_f32();
 std::vector<SpmmCfg> spmm_configs_f64();
 
-int spmm_blocks_per_sm(const SpmmCfg& c, bool weighted, bool heavy, bool fp64)
+int spmm_blocks_per_sm(const SpmmCfg& c, bool weighted, bool heavy, int prec)
 {
-    return fp64 ? spmm_blocks_per_sm_f64(c, weighted, heavy) : spmm_blocks_per_sm_f32(c, weighted, heavy);
+    if (prec == 2) return spmm_blocks_per_sm_df64(c, weighted, heavy);
+    return prec == 1 ? spmm_blocks_per_sm_f64(c, weighted, heavy) : spmm_blocks_per_sm_f32(c, weighted, heavy);
 }
+
+// Element precision of a mode: 0 FP32 vectors, 1 FP64, 2 double-float (8-byte elements
+// for 1 and 2, which share the tile configurations).
+static int mode_prec(int32_t mode) { return mode == RD_MODE_FP64 ? 1 : (mode == RD_MODE_DF64 ? 2 : 0); }
 
 std::vector<SpmmCfg> spmm_configs(bool fp64) { return fp64 ? spmm_configs_f64() : spmm_configs_f32(); }
 
@@ -110,7 +117,7 @@ static void free_graph(rd_graph* g)
     if (!g) return;
     void* ptrs[] = {g->row_ptr, g->col, g->w, g->keep_idx, g->deg64, g->invdeg64, g->deg32, g->invdeg32,
                     g->comp, g->heavy_rows, g->heavy_first, g->chunk_beg, g->chunk_end, g->task_row,
-                    g->row_order, g->entry_row, g->ws.base};
+                    g->row_order, g->entry_row, g->degdf, g->invdegdf, g->ws.base};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
@@ -318,7 +325,8 @@ static rd_status graph_build(rd_graph* g, const int64_t* row_ptr, const int32_t*
 
 // ------------------------------------------------------------- planning
 struct Plan {
-    bool fp64;
+    bool fp64;              // 8-byte vector elements (FP64 or double-float)
+    int prec = 0;           // mode_prec
     bool tuned = false;     // cfg taken from the autotuner's table
     SpmmCfg cfg;
     int64_t ld;
@@ -353,10 +361,10 @@ static int64_t tune_width(int64_t P, bool fp64, bool single)
     return w;
 }
 
-static const rd_graph::TunedCfg* find_tuned(const rd_graph* g, bool fp64, bool single, int64_t width)
+static const rd_graph::TunedCfg* find_tuned(const rd_graph* g, int prec, bool single, int64_t width)
 {
     for (const auto& t : g->tuned)
-        if (t.fp64 == (int)fp64 && t.single == (int)single && t.width == width) return &t;
+        if (t.prec == prec && t.single == (int)single && t.width == width) return &t;
     return nullptr;
 }
 
@@ -367,7 +375,7 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     if (from_table) *from_table = false;
     if (tuning_allowed(o)) {
         const bool single = plain || P == 1;
-        const rd_graph::TunedCfg* t = find_tuned(g, fp64, single, tune_width(P, fp64, single));
+        const rd_graph::TunedCfg* t = find_tuned(g, mode_prec(o.mode), single, tune_width(P, fp64, single));
         if (t) {
             if (from_table) *from_table = true;
             return t->cfg;
@@ -413,7 +421,8 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
 
 static rd_status make_plan_cfg(rd_graph* g, int64_t P, const rd_query_opts& o, const SpmmCfg& cfg, Plan* pl)
 {
-    pl->fp64 = o.mode == RD_MODE_FP64;
+    pl->prec = mode_prec(o.mode);
+    pl->fp64 = pl->prec != 0;
     pl->elem = pl->fp64 ? 8 : 4;
     pl->cfg = cfg;
     if (!cfg_known(pl->cfg, pl->fp64)) {
@@ -426,7 +435,7 @@ static rd_status make_plan_cfg(rd_graph* g, int64_t P, const rd_query_opts& o, c
     pl->nslab = (int)(pl->ld / tp);
     pl->k_max = o.k_max;
     const int rows_per_block = kWarps * pl->cfg.rpw();
-    int bps = spmm_blocks_per_sm(pl->cfg, g->weighted, false, pl->fp64);
+    int bps = spmm_blocks_per_sm(pl->cfg, g->weighted, false, pl->prec);
     if (bps < 1) bps = 1;
     int64_t gm = (int64_t)bps * g->sm_count;
     int64_t units = pl->cfg.kind == 1 ? g->ntasks : g->n;  // rows or tasks, one per row group
@@ -437,7 +446,7 @@ static rd_status make_plan_cfg(rd_graph* g, int64_t P, const rd_query_opts& o, c
     }
     gm = std::min<int64_t>(gm, (units + per_block - 1) / per_block);
     pl->grid_main = (int)std::max<int64_t>(gm, 1);
-    int bph = spmm_blocks_per_sm(pl->cfg, g->weighted, true, pl->fp64);
+    int bph = spmm_blocks_per_sm(pl->cfg, g->weighted, true, pl->prec);
     if (bph < 1) bph = 1;
     int64_t gh = (int64_t)bph * g->sm_count;
     const int chunks_per_block = kWarps * heavy_cfg(pl->cfg).rpw();
@@ -451,7 +460,7 @@ static rd_status make_plan_cfg(rd_graph* g, int64_t P, const rd_query_opts& o, c
 static rd_status make_plan(rd_graph* g, int64_t P, const rd_query_opts& o, bool plain, Plan* pl)
 {
     bool from_table = false;
-    const SpmmCfg cfg = pick_cfg(g, P, o, o.mode == RD_MODE_FP64, plain, &from_table);
+    const SpmmCfg cfg = pick_cfg(g, P, o, mode_prec(o.mode) != 0, plain, &from_table);
     RD_TRY(make_plan_cfg(g, P, o, cfg, pl));
     pl->tuned = from_table;
     return RD_OK;
@@ -622,7 +631,10 @@ static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
     a.row_ptr = g->row_ptr;
     a.col = g->col;
     a.w = g->w;
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, df64>::value) {
+        a.invdeg = g->invdegdf;
+        a.deg = g->degdf;
+    } else if constexpr (sizeof(T) == 8) {
         a.invdeg = g->invdeg64;
         a.deg = g->deg64;
     } else {
@@ -652,6 +664,26 @@ static StepArgs<T> step_args(RunCtx& c, int j, bool reduce)
     return a;
 }
 
+// Launchers by element type.
+static bool launch_spmm_t(const SpmmCfg& cfg, bool weighted, bool heavy, int grid, cudaStream_t st,
+                          const StepArgs<float>& a)
+{
+    return launch_spmm_f32(cfg, weighted, heavy, grid, st, a);
+}
+static bool launch_spmm_t(const SpmmCfg& cfg, bool weighted, bool heavy, int grid, cudaStream_t st,
+                          const StepArgs<double>& a)
+{
+    return launch_spmm_f64(cfg, weighted, heavy, grid, st, a);
+}
+static bool launch_spmm_t(const SpmmCfg& cfg, bool weighted, bool heavy, int grid, cudaStream_t st,
+                          const StepArgs<df64>& a)
+{
+    return launch_spmm_df64(cfg, weighted, heavy, grid, st, a);
+}
+static void launch_normalize_t(int grid, cudaStream_t st, const NormArgs<float>& a) { launch_normalize_f32(grid, st, a); }
+static void launch_normalize_t(int grid, cudaStream_t st, const NormArgs<double>& a) { launch_normalize_f64(grid, st, a); }
+static void launch_normalize_t(int grid, cudaStream_t st, const NormArgs<df64>& a) { launch_normalize_df64(grid, st, a); }
+
 template <typename T>
 static rd_status enqueue_spmm(RunCtx& c, int j, bool reduce)
 {
@@ -662,19 +694,11 @@ static rd_status enqueue_spmm(RunCtx& c, int j, bool reduce)
         e1 = c.ev->get();
         cudaEventRecord(e0, c.st);
     }
-    const bool fp64 = sizeof(T) == 8;
     if (c.g->n_chunks > 0) {
-        bool ok = fp64 ? launch_spmm_f64(c.cur.cfg, c.g->weighted, true, c.cur.grid_heavy, c.st,
-                                         *reinterpret_cast<StepArgs<double>*>(&a))
-                       : launch_spmm_f32(c.cur.cfg, c.g->weighted, true, c.cur.grid_heavy, c.st,
-                                         *reinterpret_cast<StepArgs<float>*>(&a));
-        if (!ok) return RD_ERR_UNSUPPORTED;
+        if (!launch_spmm_t(c.cur.cfg, c.g->weighted, true, c.cur.grid_heavy, c.st, a)) return RD_ERR_UNSUPPORTED;
         ++c.launches;
     }
-    bool ok = fp64 ? launch_spmm_f64(c.cur.cfg, c.g->weighted, false, c.cur.grid_main, c.st,
-                                     *reinterpret_cast<StepArgs<double>*>(&a))
-                   : launch_spmm_f32(c.cur.cfg, c.g->weighted, false, c.cur.grid_main, c.st,
-                                     *reinterpret_cast<StepArgs<float>*>(&a));
+    bool ok = launch_spmm_t(c.cur.cfg, c.g->weighted, false, c.cur.grid_main, c.st, a);
     if (!ok) return RD_ERR_UNSUPPORTED;
     ++c.launches;
     ++c.spmm_launches;
@@ -698,8 +722,7 @@ static void enqueue_normalize(RunCtx& c, int j, bool with_phi)
     a.phi = with_phi ? static_cast<T*>(c.b.phi) : nullptr;
     a.coef = with_phi ? static_cast<const T*>(c.b.coef_hist) + (int64_t)j * c.cur.ld : nullptr;
     a.active_prev = with_phi ? nullptr : c.b.st.act_count + j;
-    if constexpr (sizeof(T) == 8) launch_normalize_f64(c.cur.grid_norm, c.st, a);
-    else launch_normalize_f32(c.cur.grid_norm, c.st, a);
+    launch_normalize_t(c.cur.grid_norm, c.st, a);
     ++c.launches;
 }
 
@@ -714,6 +737,7 @@ static void enqueue_init(RunCtx& c, bool replay)
     a.npairs = (int)c.P;
     a.k_max = c.pl.k_max;
     a.elem_size = (int)c.pl.elem;
+    a.df = c.pl.prec == 2 ? 1 : 0;
     a.s = c.b.s;
     a.t = c.b.t;
     a.deg64 = c.g->deg64;
@@ -842,7 +866,7 @@ static rd_status launch_step_graph(RunCtx& c, const FinArgs& base)
     key.append(reinterpret_cast<const char*>(&sa), sizeof(sa));
     key.append(reinterpret_cast<const char*>(&fa), sizeof(fa));
     key.append(reinterpret_cast<const char*>(&na), sizeof(na));
-    key.push_back(sizeof(T) == 8 ? 'd' : 'f');
+    key.push_back(std::is_same<T, df64>::value ? 'w' : (sizeof(T) == 8 ? 'd' : 'f'));
     cudaGraphExec_t exec = nullptr;
     for (const auto& kv : g->graphs)
         if (kv.first == key) {
@@ -854,20 +878,11 @@ static rd_status launch_step_graph(RunCtx& c, const FinArgs& base)
         cudaStream_t cs = g->capture_stream;
         RD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         bool ok = true;
-        if (heavy)
-            ok = sizeof(T) == 8 ? launch_spmm_f64(c.cur.cfg, g->weighted, true, c.cur.grid_heavy, cs,
-                                                  *reinterpret_cast<const StepArgs<double>*>(&sa))
-                                : launch_spmm_f32(c.cur.cfg, g->weighted, true, c.cur.grid_heavy, cs,
-                                                  *reinterpret_cast<const StepArgs<float>*>(&sa));
-        if (ok)
-            ok = sizeof(T) == 8 ? launch_spmm_f64(c.cur.cfg, g->weighted, false, c.cur.grid_main, cs,
-                                                  *reinterpret_cast<const StepArgs<double>*>(&sa))
-                                : launch_spmm_f32(c.cur.cfg, g->weighted, false, c.cur.grid_main, cs,
-                                                  *reinterpret_cast<const StepArgs<float>*>(&sa));
+        if (heavy) ok = launch_spmm_t(c.cur.cfg, g->weighted, true, c.cur.grid_heavy, cs, sa);
+        if (ok) ok = launch_spmm_t(c.cur.cfg, g->weighted, false, c.cur.grid_main, cs, sa);
         if (ok) {
             launch_finalize(cs, fa);
-            if constexpr (sizeof(T) == 8) launch_normalize_f64(c.cur.grid_norm, cs, na);
-            else launch_normalize_f32(c.cur.grid_norm, cs, na);
+            launch_normalize_t(c.cur.grid_norm, cs, na);
             launch_step_advance(cs, c.b.step_dev, c.pl.k_max);
         }
         cudaGraph_t graph = nullptr;
@@ -912,6 +927,7 @@ static rd_status run_forward(RunCtx& c)
     fa.deflate = (c.o.flags & RD_Q_NO_DEFLATE) ? 0 : 1;
     fa.fixed_k = (c.o.flags & RD_Q_FIXED_K) ? 1 : 0;
     fa.fp64 = sizeof(T) == 8;
+    fa.df = std::is_same<T, df64>::value ? 1 : 0;
     fa.rel_tol = c.o.rel_tol;
     fa.resid_tol = c.o.resid_tol;
     fa.est_delayed = (c.o.flags & RD_Q_EST_DELAYED) ? 1 : 0;
@@ -1098,7 +1114,7 @@ static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t
         set_error("kernel must be 0, 1, 2, 3 or 4");
         return RD_ERR_INVALID_ARG;
     }
-    if (o->mode != RD_MODE_FP64 && o->mode != RD_MODE_FP32V_FP64S) {
+    if (o->mode != RD_MODE_FP64 && o->mode != RD_MODE_FP32V_FP64S && o->mode != RD_MODE_DF64) {
         set_error("unknown mode");
         return RD_ERR_INVALID_ARG;
     }
@@ -1194,7 +1210,8 @@ static rd_status ensure_tuned(rd_graph* g, int64_t P, const rd_query_opts& o, bo
                               cudaStream_t st)
 {
     if (!tuning_allowed(o) || P < 1 || g->n == 0) return RD_OK;
-    const bool fp64 = o.mode == RD_MODE_FP64;
+    const int prec = mode_prec(o.mode);
+    const bool fp64 = prec != 0;
     const bool single = plain || P == 1;
     std::vector<int64_t> widths{tune_width(P, fp64, single)};
     const int64_t tmin = fp64 ? 8 : 16;
@@ -1202,13 +1219,14 @@ static rd_status ensure_tuned(rd_graph* g, int64_t P, const rd_query_opts& o, bo
         for (int64_t w = widths[0] / 2; w >= tmin; w /= 2) widths.push_back(w);
     EventPool ev;
     for (int64_t w : widths) {
-        if (find_tuned(g, fp64, single, w)) continue;
+        if (find_tuned(g, prec, single, w)) continue;
         rd_graph::TunedCfg best;
         best.us = -1.f;
         for (const SpmmCfg& cfg : tune_candidates(g, w, fp64, single)) {
             float us = 0.f;
-            rd_status r = fp64 ? time_cfg<double>(g, w, o, cfg, st, ev, &us)
-                               : time_cfg<float>(g, w, o, cfg, st, ev, &us);
+            rd_status r = prec == 2 ? time_cfg<df64>(g, w, o, cfg, st, ev, &us)
+                          : (prec == 1 ? time_cfg<double>(g, w, o, cfg, st, ev, &us)
+                                       : time_cfg<float>(g, w, o, cfg, st, ev, &us));
             if (r == RD_ERR_OOM) continue;  // a wider padding that does not fit is not a candidate
             if (r < 0) return r;
             if (best.us < 0.f || us < best.us) {
@@ -1217,7 +1235,7 @@ static rd_status ensure_tuned(rd_graph* g, int64_t P, const rd_query_opts& o, bo
             }
         }
         if (best.us < 0.f) continue;  // nothing fitted: the fixed rule decides
-        best.fp64 = fp64 ? 1 : 0;
+        best.prec = prec;
         best.single = single ? 1 : 0;
         best.width = w;
         g->tuned.push_back(best);
@@ -1235,6 +1253,13 @@ static rd_status prepare_run(RunCtx& c, rd_graph* g, int64_t P, const rd_query_o
     c.profile = (o.flags & RD_Q_PROFILE) != 0;
     c.compact = compact;
     c.lagged_polls = lagged_polls && c.ev != nullptr;
+    if (mode_prec(o.mode) == 2 && !g->degdf && g->n > 0) {  // double-float degrees, once per graph
+        RD_CUDA(cudaMalloc((void**)&g->degdf, sizeof(df64) * g->n));
+        RD_CUDA(cudaMalloc((void**)&g->invdegdf, sizeof(df64) * g->n));
+        const int grid = std::max(1, std::min(g->sm_count * 8, (int)((g->n + 255) / 256)));
+        launch_split_df(st, grid, g->n, g->deg64, g->degdf);
+        launch_split_df(st, grid, g->n, g->invdeg64, g->invdegdf);
+    }
     RD_TRY(ensure_tuned(g, P, o, plain, compact, st));
     RD_TRY(make_plan(g, P, o, plain, &c.pl));
     c.cur = c.pl;
@@ -1257,7 +1282,8 @@ static rd_status query_batch(rd_graph* g, const int32_t* s, const int32_t* t, in
     RD_TRY(prepare_run(c, g, P, o, plain, false, st, compact && !plain, lagged_polls));
     c.onchip = (o.flags & RD_Q_NO_ONCHIP) == 0 && onchip_smem_bytes(g->n, (int)c.pl.elem) <= 220 * 1024;
     RD_TRY(stage_pairs(c, s, t));
-    rd_status rs = o.mode == RD_MODE_FP64 ? run_forward<double>(c) : run_forward<float>(c);
+    rd_status rs = c.pl.prec == 2 ? run_forward<df64>(c)
+                   : (c.pl.prec == 1 ? run_forward<double>(c) : run_forward<float>(c));
     if (rs < 0) return rs;
     RD_TRY(finish_outputs(c, r_out, iters_out, err_out, status_out, call_status));
     record_stats(c);
@@ -1518,6 +1544,7 @@ rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t 
     g_last_error.clear();
     rd_query_opts o;
     RD_TRY(validate_common(g, s, t, npairs, opts, &o));
+    if (o.mode == RD_MODE_DF64) o.mode = RD_MODE_FP64;  // double-float vectors: rd_query only
     if (!grad_w_out && g->nnz_in > 0) {
         set_error("grad_w_out must not be NULL");
         return RD_ERR_INVALID_ARG;
@@ -1611,6 +1638,7 @@ extern "C" rd_status rd_potential(rd_graph* g, const int32_t* s, const int32_t* 
     g_last_error.clear();
     rd_query_opts o;
     RD_TRY(validate_common(g, s, t, npairs, opts, &o));
+    if (o.mode == RD_MODE_DF64) o.mode = RD_MODE_FP64;  // double-float vectors: rd_query only
     if (npairs > 0 && !phi_out) {
         set_error("phi_out must not be NULL");
         return RD_ERR_INVALID_ARG;
@@ -1674,6 +1702,7 @@ extern "C" rd_status rd_flow(rd_graph* g, const int32_t* s, const int32_t* t, in
     g_last_error.clear();
     rd_query_opts o;
     RD_TRY(validate_common(g, s, t, npairs, opts, &o));
+    if (o.mode == RD_MODE_DF64) o.mode = RD_MODE_FP64;  // double-float vectors: rd_query only
     if (npairs > 0 && g->nnz_in > 0 && !flow_out) {
         set_error("flow_out must not be NULL");
         return RD_ERR_INVALID_ARG;
@@ -1775,6 +1804,7 @@ extern "C" rd_status rd_power_method(rd_graph* g, const int32_t* s, const int32_
         return RD_ERR_INVALID_ARG;
     }
     RD_TRY(validate_common(g, s, t, npairs, &o, &o));
+    if (o.mode == RD_MODE_DF64) o.mode = RD_MODE_FP64;  // double-float vectors: rd_query only
     if (npairs > 0 && !r_out) {
         set_error("r_out must not be NULL");
         return RD_ERR_INVALID_ARG;
@@ -1916,6 +1946,7 @@ extern "C" rd_status rd_query_noalloc(int64_t n, int64_t nnz, const int64_t* row
 
     rd_query_opts o;
     RD_TRY(validate_common(&g, s, t, npairs, opts, &o));
+    if (o.mode == RD_MODE_DF64) o.mode = RD_MODE_FP64;  // double-float vectors: rd_query only
     o.flags &= ~RD_Q_PROFILE;  // no event objects
     // no timing runs (they could need a larger workspace) and no graph objects
     o.flags |= RD_Q_NO_TUNE | RD_Q_NO_GRAPH;

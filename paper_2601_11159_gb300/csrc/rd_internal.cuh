@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/rd.h"
+#include "df64.cuh"
 
 namespace rd {
 
@@ -163,6 +164,7 @@ struct FinArgs {
     int elem_size;
     const int32_t* step_dev;            // nullable: step index from device memory (graph replay);
     int64_t cf_stride;                  // then cf_step/cf_next advance by j * cf_stride
+    int df;                             // 1: coefficients are stored as double-float pairs
 };
 
 // Whole recurrence of one pair per CTA with q_{i-1}, q_i and W in shared memory (graphs
@@ -243,6 +245,8 @@ struct rd_graph {
     double* invdeg64 = nullptr;
     float* deg32 = nullptr;
     float* invdeg32 = nullptr;
+    rd::df64* degdf = nullptr;        // double-float copies (built on first use)
+    rd::df64* invdegdf = nullptr;
     double sumdeg = 0.0;
     int32_t* comp = nullptr;
     int32_t ncomp = 0;
@@ -268,7 +272,7 @@ struct rd_graph {
     int64_t l2_bytes = 0;             // device L2 size
     // SpMM configurations chosen by the autotuner on this graph, per width class
     struct TunedCfg {
-        int fp64 = 0, single = 0;     // precision; single-column SpMV (plain / one pair) or batched
+        int prec = 0, single = 0;     // element precision (0 FP32, 1 FP64, 2 double-float); one column or many
         int64_t width = 0;            // width class (power-of-two tile holding the pairs; 1 if single)
         rd::SpmmCfg cfg;
         float us = 0.f;               // measured time of one SpMM launch pair
@@ -286,13 +290,18 @@ namespace rd {
 // Returns false if the configuration is not instantiated.
 bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
                      const StepArgs<float>& a);
+bool launch_spmm_df64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
+                      const StepArgs<df64>& a);
 bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
                      const StepArgs<double>& a);
-int spmm_blocks_per_sm(const SpmmCfg& c, bool weighted, bool heavy, bool fp64);
+// prec: 0 FP32 vectors, 1 FP64, 2 double-float
+int spmm_blocks_per_sm(const SpmmCfg& c, bool weighted, bool heavy, int prec);
 std::vector<SpmmCfg> spmm_configs(bool fp64);
 
 void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a);
 void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a);
+void launch_normalize_df64(int grid, cudaStream_t st, const NormArgs<df64>& a);
+void launch_split_df(cudaStream_t st, int grid, int64_t n, const double* src, df64* dst);
 void launch_finalize(cudaStream_t st, const FinArgs& a);
 // Advance the device step index by one, saturating at `limit` (end of a replayed step).
 void launch_step_advance(cudaStream_t st, int32_t* step, int limit);
@@ -300,6 +309,7 @@ void launch_step_advance(cudaStream_t st, int32_t* step, int limit);
 struct InitArgs {
     int64_t n, ld;
     int npairs, k_max, elem_size;
+    int df;                       // 1: vectors are double-float pairs (elem_size 8)
     const int32_t* s;
     const int32_t* t;
     const double* deg64;

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include "df64.cuh"
 #include "rd_internal.cuh"
 
 namespace rd {
@@ -205,6 +206,13 @@ struct Acc<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
+template <>
+struct Acc<df64> {
+    df64 s = df64(0);
+    __device__ __forceinline__ void add(df64 x) { s += x; }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+
 // Independent gathers in flight per lane per round: 8 for 16-byte lanes, 4 for wider ones.
 #ifndef RD_ROWS_UNROLL
 #define RD_ROWS_UNROLL 8
@@ -261,7 +269,7 @@ __device__ __forceinline__ void reduce_nzl(T (&acc)[VEC], unsigned mask)
 #pragma unroll
     for (int off = GS; off < GS * NZL; off <<= 1) {
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) acc[i] += __shfl_xor_sync(mask, acc[i], off);
+        for (int i = 0; i < VEC; ++i) acc[i] += shfl_xor_t(mask, acc[i], off);
     }
 }
 
@@ -432,6 +440,20 @@ struct SmemAcc<double, VEC> {
     }
     __device__ __forceinline__ void add(int q, int i, double x) { p[(q * VEC + i) * kBlock] += x; }
     __device__ __forceinline__ double value(int q, int i) const { return p[(q * VEC + i) * kBlock]; }
+};
+
+template <int VEC>
+struct SmemAcc<df64, VEC> {
+    static constexpr int kWords = 3 * VEC * 2;  // 32-bit words per thread
+    df64* p;
+    __device__ __forceinline__ void init(float* base)
+    {
+        p = reinterpret_cast<df64*>(base) + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < 3 * VEC; ++k) p[k * kBlock] = df64(0);
+    }
+    __device__ __forceinline__ void add(int q, int i, df64 x) { p[(q * VEC + i) * kBlock] += x; }
+    __device__ __forceinline__ double value(int q, int i) const { return (double)p[(q * VEC + i) * kBlock]; }
 };
 
 template <typename T, int VEC, int TP>
@@ -749,8 +771,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
                         if (e >= e_end) break;
                         while (e >= row_end) {  // the stream leaves `row`
                             const int wi = row - w0;
-                            const T invd = __shfl_sync(mask, my_invd, wi, GS);
-                            const T du = __shfl_sync(mask, my_deg, wi, GS);
+                            const T invd = shfl_t(mask, my_invd, wi, GS);
+                            const T du = shfl_t(mask, my_deg, wi, GS);
                             row_epilogue_b<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, rb, sacc);
 #pragma unroll
                             for (int i = 0; i < VEC; ++i) acc[i] = T(0);
@@ -778,8 +800,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
             // last row of the task (and any rows without nonzeros after it)
             while (row < r1) {
                 const int wi = row - w0;
-                const T invd = __shfl_sync(mask, my_invd, wi, GS);
-                const T du = __shfl_sync(mask, my_deg, wi, GS);
+                const T invd = shfl_t(mask, my_invd, wi, GS);
+                const T du = shfl_t(mask, my_deg, wi, GS);
                 row_epilogue_b<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, rb, sacc);
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) acc[i] = T(0);
@@ -830,7 +852,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_tasks(const StepArgs<T> a)
             T acc[1] = {T(0)};
             heavy_row_sum<T, 1, 32>(a, r0, 0, lane, acc);
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], off);
+            for (int off = 16; off > 0; off >>= 1) acc[0] += shfl_xor_t(0xffffffffu, acc[0], off);
             if (lane == 0) {
                 T qp[1], qc[1], bt1[1] = {bt};
                 qp[0] = a.qprev_w[r0];
@@ -854,7 +876,9 @@ __global__ void __launch_bounds__(kBlock) k_spmv_tasks(const StepArgs<T> a)
                 x[u] = T(0);
                 if (idx[u] < cnt) {
                     const int64_t j = __ldg(a.col + e0 + idx[u]);
-                    x[u] = __ldg(a.qcur + j);
+                    T xv[1];
+                    ld_gather<T, 1>(xv, a.qcur + j);
+                    x[u] = xv[0];
                 }
             }
 #pragma unroll

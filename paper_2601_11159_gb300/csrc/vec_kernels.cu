@@ -65,7 +65,8 @@ __global__ void k_init(const InitArgs a)
 void launch_init(cudaStream_t st, const InitArgs& a)
 {
     const int nb = (a.npairs + 127) / 128;
-    if (a.elem_size == 8) k_init<double><<<nb, 128, 0, st>>>(a);
+    if (a.df) k_init<df64><<<nb, 128, 0, st>>>(a);
+    else if (a.elem_size == 8) k_init<double><<<nb, 128, 0, st>>>(a);
     else k_init<float><<<nb, 128, 0, st>>>(a);
 }
 
@@ -259,7 +260,8 @@ void launch_finalize(cudaStream_t st, const FinArgs& a)
 {
     const int cb = fin_cols_per_block(a.ld);
     const int nb = (int)((a.ld + cb - 1) / cb);
-    if (a.elem_size == 8) k_finalize<double><<<nb, 256, 0, st>>>(a);
+    if (a.df) k_finalize<df64><<<nb, 256, 0, st>>>(a);
+    else if (a.elem_size == 8) k_finalize<double><<<nb, 256, 0, st>>>(a);
     else k_finalize<float><<<nb, 256, 0, st>>>(a);
 }
 
@@ -343,6 +345,19 @@ void launch_step_advance(cudaStream_t st, int32_t* step, int limit) { k_step_adv
 
 void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a) { launch_norm<float>(grid, st, a); }
 void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a) { launch_norm<double>(grid, st, a); }
+void launch_normalize_df64(int grid, cudaStream_t st, const NormArgs<df64>& a) { launch_norm<df64>(grid, st, a); }
+
+// Double-float copy of an FP64 array (degrees and their inverses for RD_MODE_DF64).
+__global__ void k_split_df(int64_t n, const double* __restrict__ src, df64* __restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = df64(src[i]);
+}
+
+void launch_split_df(cudaStream_t st, int grid, int64_t n, const double* src, df64* dst)
+{
+    k_split_df<<<grid, 256, 0, st>>>(n, src, dst);
+}
 
 // ---------------------------------------------------------------- output
 __global__ void k_output(const OutArgs a)

@@ -525,3 +525,43 @@ def test_error_estimate_stop_meets_rel_tol(rd, family):
         if family in ("chunglu", "rmat", "ba"):
             old = G.query(s, t, mode="fp64", k_max=5000, rel_tol=tol, estimate="delayed")
             assert np.all(res.iters <= old.iters)
+
+
+@pytest.mark.parametrize("kernel", ["tuned", "group", "stream", "tasks"])
+def test_double_float_mode_vs_oracle(rd, kernel):
+    """RD_MODE_DF64 (vectors as FP32 pairs, FP64-class accuracy on the FP32 units): fixed-k
+    estimates equal the FP64 oracle's, converged values equal the dense pseudo-inverse, on
+    unweighted and weighted graphs, batched (with compaction and graph replay) and plain."""
+    for g in (F.grid_deleted(24, 0.05, 9), F.random_connected(300, 900, 31, "lognormal")):
+        s, t = F.random_pairs(g.n, 9, 2)
+        G = rd.Graph.from_csr(g)
+        plain = kernel == "tasks"
+        kw = dict(kernel=kernel, onchip=False, plain=plain)
+        for k in (1, 3, 17, 40):
+            ref = np.array([lanczos.lanczos_pair(g, int(a), int(b), k_max=k)["r"] for a, b in zip(s, t)])
+            res = G.query(s, t, mode="df64", k_max=k, fixed_k=True, **kw)
+            assert rel(res.r, ref).max() < 1e-11, (k, rel(res.r, ref).max())
+        exact = dense.DenseRD.of(g).r(s, t)
+        res = G.query(s, t, mode="df64", k_max=2000, rel_tol=0.0, resid_tol=1e-12, **kw)
+        assert np.all(res.status == 0)
+        assert rel(res.r, exact).max() < FP64_TOL
+        if not plain:
+            gb = G.query(s, t, mode="df64", k_max=2000, rel_tol=0.0, resid_tol=1e-12, graph=False, **kw)
+            assert np.array_equal(gb.r, res.r)
+
+
+def test_double_float_mode_batched_chunglu(rd):
+    """Batched double-float query with the error-estimate stop, compaction and the tuned
+    kernels on a power-law graph: within 1e-9 of the oracle; the other entry points run the
+    mode as FP64."""
+    g, s, t = W.chunglu(30000, 2.1, 20.0, 300000, 100, 23)
+    G = rd.Graph.from_csr(g)
+    ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=300, stop_tol=1e-15, threads=0)
+    res = G.query(s, t, mode="df64", k_max=300, rel_tol=0.0, resid_tol=1e-11)
+    assert G.last_stats()["compactions"] >= 1
+    assert rel(res.r, ref).max() < FP64_TOL
+    r64 = G.query(s, t, mode="fp64", k_max=300, rel_tol=0.0, resid_tol=1e-11).r
+    assert rel(res.r, r64).max() < 1e-10
+    gd, rd_ = G.edge_grad(s[:4], t[:4], None, mode="df64", k_max=300, rel_tol=0.0, resid_tol=1e-11)
+    g6, r6 = G.edge_grad(s[:4], t[:4], None, mode="fp64", k_max=300, rel_tol=0.0, resid_tol=1e-11)
+    assert np.array_equal(gd, g6) and np.array_equal(rd_, r6)
