@@ -517,80 +517,6 @@ __device__ __forceinline__ void row_epilogue_s(const StepArgs<T>& a, int64_t row
     }
 }
 
-// One step: W = D^{-1} W_adj q_i - beta_i q_{i-1} written over q_{i-1}, plus block
-// partial sums of sum_u d_u W q_i, sum_u d_u W^2 and sum_u d_u W per column.
-// Blocks per SM the row-group kernel is compiled for. With narrow lanes (16 bytes) the
-// Kahan accumulators of the three reductions live in shared memory (SmemAcc) instead of
-// registers, which lets more warps be resident to keep gathers in flight.
-#ifndef RD_GROUP_MINB
-#define RD_GROUP_MINB 4
-#endif
-#ifndef RD_GROUP_SMEM
-#define RD_GROUP_SMEM 1
-#endif
-template <typename T, int VEC>
-inline constexpr bool kGroupSmemAcc = RD_GROUP_SMEM && (int)sizeof(T) * VEC <= 16;
-template <typename T, int VEC>
-inline constexpr int kGroupMinBlocks = kGroupSmemAcc<T, VEC> ? RD_GROUP_MINB : 1;
-
-template <typename T, int VEC, int GS, int NZL, bool WEIGHTED>
-__global__ void __launch_bounds__(kBlock, kGroupMinBlocks<T, VEC>) k_spmm(const StepArgs<T> a)
-{
-    constexpr int TP = VEC * GS;
-    constexpr int RPW = 32 / (GS * NZL);
-    constexpr bool kSmem = kGroupSmemAcc<T, VEC>;
-    __shared__ double red[kWarps][TP];
-    __shared__ __align__(16) float sacc_buf[kSmem ? SmemAcc<T, VEC>::kWords * kBlock : 1];
-    if (step_inactive(a)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cl = lane % GS, zl = (lane / GS) % NZL;
-    const int rs = lane / (GS * NZL);
-    const int li = lane % (GS * NZL);
-    const unsigned mask = group_mask<GS, NZL>(lane);
-    const int64_t nslots = (int64_t)gridDim.x * kWarps * RPW;
-    const int64_t slot0 = ((int64_t)blockIdx.x * kWarps + warp) * RPW + rs;
-    const int nslab = (int)(a.ld / TP);
-    const int64_t ld = a.ld;
-
-    for (int slab = 0; slab < nslab; ++slab) {
-        const int64_t c0 = (int64_t)slab * TP + cl * VEC;
-        T bt[VEC];
-        ld_plain<T, VEC>(bt, step_cf_beta(a) + c0);
-        Acc<T> sA[VEC], sB[VEC], sC[VEC];
-        SmemAcc<T, VEC> sacc;
-        if constexpr (kSmem) sacc.init(sacc_buf);
-
-        for (int64_t i = slot0; i < a.n; i += nslots) {
-            const int64_t row = a.row_order ? (int64_t)a.row_order[i] : i;
-            const int64_t beg = a.row_ptr[row], end = a.row_ptr[row + 1];
-            T acc[VEC], qp[VEC], qc[VEC];
-#pragma unroll
-            for (int i = 0; i < VEC; ++i) acc[i] = T(0);
-            if (zl == 0) {  // own-row operands of the epilogue, issued before the gather
-                ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
-                ld_gather<T, VEC>(qc, a.qcur + row * ld + c0);
-            }
-            if (end - beg > a.heavy_thr) {
-                heavy_row_sum<T, VEC, NZL>(a, row, c0, zl, acc);
-            } else {
-                gather_row<T, VEC, GS, NZL, kUnroll<T, VEC>, WEIGHTED>(a, beg, end, c0, li, zl, mask, acc);
-            }
-            reduce_nzl<GS, NZL>(acc, mask);
-            if (zl == 0) {
-                if constexpr (kSmem) row_epilogue_s<T, VEC>(a, row, c0, a.invdeg[row], a.deg[row], acc, bt, qp, qc, sacc);
-                else row_epilogue<T, VEC>(a, row, c0, a.invdeg[row], a.deg[row], acc, bt, qp, qc, sA, sB, sC);
-            }
-        }
-
-        if constexpr (kSmem) {
-            if (a.do_reduce) block_partials_s<T, VEC, GS * NZL, TP>(a, sacc, red, slab, lane, warp, cl);
-            __syncthreads();  // the accumulators are re-initialised by the next slab
-        } else {
-            if (a.do_reduce) block_partials<T, VEC, GS * NZL, TP>(a, sA, sB, sC, red, slab, lane, warp, cl);
-        }
-    }
-}
-
 #ifndef RD_ROWS_MINB
 #define RD_ROWS_MINB 2
 #endif
@@ -653,6 +579,82 @@ __device__ __forceinline__ void row_epilogue_b(const StepArgs<T>& a, int row, in
         if (++rb.cnt == RD_ROWS_BATCH) rb.flush(sacc);
     }
 }
+
+// One step: W = D^{-1} W_adj q_i - beta_i q_{i-1} written over q_{i-1}, plus block
+// partial sums of sum_u d_u W q_i, sum_u d_u W^2 and sum_u d_u W per column.
+// Blocks per SM the row-group kernel is compiled for. With narrow lanes (16 bytes) the
+// Kahan accumulators of the three reductions live in shared memory (SmemAcc) instead of
+// registers, which lets more warps be resident to keep gathers in flight.
+#ifndef RD_GROUP_MINB
+#define RD_GROUP_MINB 4
+#endif
+#ifndef RD_GROUP_SMEM
+#define RD_GROUP_SMEM 1
+#endif
+template <typename T, int VEC>
+inline constexpr bool kGroupSmemAcc = RD_GROUP_SMEM && (int)sizeof(T) * VEC <= 16;
+template <typename T, int VEC>
+inline constexpr int kGroupMinBlocks = kGroupSmemAcc<T, VEC> ? RD_GROUP_MINB : 1;
+
+
+template <typename T, int VEC, int GS, int NZL, bool WEIGHTED>
+__global__ void __launch_bounds__(kBlock, kGroupMinBlocks<T, VEC>) k_spmm(const StepArgs<T> a)
+{
+    constexpr int TP = VEC * GS;
+    constexpr int RPW = 32 / (GS * NZL);
+    constexpr bool kSmem = kGroupSmemAcc<T, VEC>;
+    __shared__ double red[kWarps][TP];
+    __shared__ __align__(16) float sacc_buf[kSmem ? SmemAcc<T, VEC>::kWords * kBlock : 1];
+    if (step_inactive(a)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cl = lane % GS, zl = (lane / GS) % NZL;
+    const int rs = lane / (GS * NZL);
+    const int li = lane % (GS * NZL);
+    const unsigned mask = group_mask<GS, NZL>(lane);
+    const int64_t nslots = (int64_t)gridDim.x * kWarps * RPW;
+    const int64_t slot0 = ((int64_t)blockIdx.x * kWarps + warp) * RPW + rs;
+    const int nslab = (int)(a.ld / TP);
+    const int64_t ld = a.ld;
+
+    for (int slab = 0; slab < nslab; ++slab) {
+        const int64_t c0 = (int64_t)slab * TP + cl * VEC;
+        T bt[VEC];
+        ld_plain<T, VEC>(bt, step_cf_beta(a) + c0);
+        Acc<T> sA[VEC], sB[VEC], sC[VEC];
+        SmemAcc<T, VEC> sacc;
+        if constexpr (kSmem) sacc.init(sacc_buf);
+
+        for (int64_t i = slot0; i < a.n; i += nslots) {
+            const int64_t row = a.row_order ? (int64_t)a.row_order[i] : i;
+            const int64_t beg = a.row_ptr[row], end = a.row_ptr[row + 1];
+            T acc[VEC], qp[VEC], qc[VEC];
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[i] = T(0);
+            if (zl == 0) {  // own-row operands of the epilogue, issued before the gather
+                ld_stream<T, VEC>(qp, a.qprev_w + row * ld + c0);
+                ld_gather<T, VEC>(qc, a.qcur + row * ld + c0);
+            }
+            if (end - beg > a.heavy_thr) {
+                heavy_row_sum<T, VEC, NZL>(a, row, c0, zl, acc);
+            } else {
+                gather_row<T, VEC, GS, NZL, kUnroll<T, VEC>, WEIGHTED>(a, beg, end, c0, li, zl, mask, acc);
+            }
+            reduce_nzl<GS, NZL>(acc, mask);
+            if (zl == 0) {
+                if constexpr (kSmem) row_epilogue_s<T, VEC>(a, row, c0, a.invdeg[row], a.deg[row], acc, bt, qp, qc, sacc);
+                else row_epilogue<T, VEC>(a, row, c0, a.invdeg[row], a.deg[row], acc, bt, qp, qc, sA, sB, sC);
+            }
+        }
+
+        if constexpr (kSmem) {
+            if (a.do_reduce) block_partials_s<T, VEC, GS * NZL, TP>(a, sacc, red, slab, lane, warp, cl);
+            __syncthreads();  // the accumulators are re-initialised by the next slab
+        } else {
+            if (a.do_reduce) block_partials<T, VEC, GS * NZL, TP>(a, sA, sB, sC, red, slab, lane, warp, cl);
+        }
+    }
+}
+
 
 __device__ __forceinline__ void prefetch_l1(const void* p)
 {
