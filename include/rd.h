@@ -190,7 +190,7 @@ rd_status rd_query(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npai
 /* Gradient of sum_p grad_r[p] * r(s_p, t_p) with respect to the stored edge weights.
  * For stored entry e = (u -> v): grad_w_out[e] = 1/2 * sum_p grad_r[p] * dr_p/dw_uv with
  * dr/dw_uv = -(phi(u) - phi(v))^2 and phi = sqrt(1/d_s+1/d_t) D^{-1/2} V_k (I-T_k)^{-1} e_1,
- * the Lanczos potential of Section 6.3 (Algorithm 5, first line). Both stored copies of an
+ * the Lanczos potential of Section 6.3 (the one Algorithm 5 starts from). Both stored copies of an
  * edge get the same value, so moving both copies by delta changes the objective by
  * delta * (sum of the two). phi is rebuilt by a second Lanczos pass that replays the
  * stored alpha/beta (no basis V_k is kept).
@@ -203,7 +203,7 @@ rd_status rd_edge_grad(rd_graph* g, const int32_t* s, const int32_t* t, int64_t 
                        const double* grad_r, const rd_query_opts* opts, float* grad_w_out,
                        double* r_out, void* stream);
 
-/* Lanczos potentials (Section 6.3, Definition electric_flow and Algorithm 5, first line):
+/* Lanczos potentials (Section 6.3, Definition electric_flow and Algorithm 5):
  * phi_out is float[npairs][n] (pair-major), host or device; phi_p is defined up to an
  * additive constant (the library's is orthogonal to the degree vector). Edge flows are
  * f(e) = phi(u) - phi(v). r_out as rd_query (nullable). Errors as rd_query. */
@@ -230,7 +230,7 @@ rd_status rd_power_method(rd_graph* g, const int32_t* s, const int32_t* t, int64
 
 /* Electric flows (Section 6.3, Definition electric_flow): for every stored entry e = (u -> v),
  * flow_out[p][e] = phi_p(u) - phi_p(v), with phi_p the Lanczos potential of pair p as in
- * rd_potential (Algorithm 5, second line). The current through the edge is w_e * flow.
+ * rd_potential (Section 6.3, Algorithm 5). The current through the edge is w_e * flow.
  *  flow_out : float[npairs][nnz] (nnz as passed to create, caller's entry order; entries that
  *             were self-loops get 0), host or device.
  *  r_out    : double[npairs] or NULL. Errors as rd_query. */
@@ -266,7 +266,7 @@ rd_status rd_query_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const
                            const rd_query_opts* opts, double* r_out, int32_t* iters_out, void* stream);
 
 /* SpMM autotuner. No counterpart in the paper: it picks the right-hand-side tile, the rows
- * per warp and the kernel of the SpMM step (Algorithm 3, line 3) for this graph and GPU by
+ * per warp and the kernel of the SpMM step of Algorithm 3 for this graph and GPU by
  * timing, not by a fixed rule. For a query of npairs pairs in opts->mode it times every
  * instantiated candidate (tiles from a quarter of the pair count's power-of-two width up to
  * that width; the row-stream kernel and the row-group kernel with 1, 2 or 4 nonzero lanes

@@ -1,5 +1,5 @@
 """Oracle, Lanczos part: Python access to the plain C FP64 Lanczos of ``lanczos_ref.c``
-(Section 3, Algorithm 3; potential from Section 6.3, Algorithm 5, first line).
+(Section 3, Algorithm 3; potential from Section 6.3, Algorithm 5).
 
 TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the benchmark's
 CPU baseline; never by the product library. It is compiled with gcc on first use

@@ -29,7 +29,7 @@
  *    when |rhat_k - rhat_{k-1}| <= stop_tol * rhat_k (stop_tol = 0: run to k_max).
  *  - s == t returns 0 without iterating.
  *
- * The potential of Section 6.3 (Algorithm 5, first line),
+ * The potential of Section 6.3 (the one Algorithm 5 starts from),
  *   phi = sqrt(1/d_s + 1/d_t) * D^{-1/2} V_k (I - T_k)^{-1} e_1,
  * is formed from the stored basis V_k.
  */

@@ -1,6 +1,6 @@
-// SpMM / SpMV step of the batched Lanczos recurrence (Algorithm 3, line "v_{i+1} =
-// Ahat v_i - beta_i v_{i-1}", Eq. (lz_recurrence)), fused with the partial sums of
-// alpha_i = <w, v_i> (line 4), ||w||^2 (line 6) and the component of w along D^{1/2}1.
+// SpMM / SpMV step of the batched Lanczos recurrence (Algorithm 3: the product
+// w = Ahat v_i - beta_i v_{i-1} of the three-term recurrence, Section 3), fused with the
+// partial sums of alpha_i = <w, v_i>, ||w||^2 and the component of w along D^{1/2}1.
 //
 // Vectors are kept in q-space, q = D^{-1/2} v, so that
 //   D^{-1/2}(Ahat v - beta v') = D^{-1} W q - beta q'        (row u: (1/d_u) sum_e w_e q[col_e])

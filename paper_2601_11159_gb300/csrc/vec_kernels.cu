@@ -1,8 +1,8 @@
 // Per-step vector and per-pair scalar kernels of the batched Lanczos iteration:
-// start vector (Algorithm 3, first line), FP64 finalisation of alpha/beta with an
-// O(1)-per-step LDL^T update of I - T_k (Eq. (approx_formula)), normalisation
-// (line "v_{i+1} = v_{i+1}/beta_{i+1}"), output, the tridiagonal solve for the
-// potential (Algorithm 5, first line) and the edge-weight gradient.
+// start vector (Algorithm 3), FP64 finalisation of alpha/beta with an O(1)-per-step
+// LDL^T update of I - T_k (the quadratic form of Section 3), normalisation
+// v_{i+1} = w / beta_{i+1} (Algorithm 3), output, the tridiagonal solve for the
+// potential of Algorithm 5 and the edge-weight gradient.
 #include <math.h>
 
 #include "spmm.cuh"
@@ -383,7 +383,7 @@ void launch_output(cudaStream_t st, const OutArgs& a)
 // z = (I - T_k)^{-1} e_1 per pair from the stored alpha_1..alpha_k, beta_2..beta_k by
 // forward elimination and back substitution (I - T_k is SPD, so no pivoting);
 // coef_j = ||b|| z_j is the weight of q_j in the potential
-// phi = ||b|| D^{-1/2} V_k z (Algorithm 5, first line). Also writes gbar[p], the upstream
+// phi = ||b|| D^{-1/2} V_k z (the potential of Algorithm 5). Also writes gbar[p], the upstream
 // gradient of pair p (0 for pairs without a finite result and for padding columns).
 template <typename T>
 __global__ void k_zsolve(const ZsolveArgs a)
