@@ -231,6 +231,39 @@ __device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t beg, in
     constexpr int G = GS * NZL;
     const T* __restrict__ q = a.qcur + c0;
     const int64_t ld = a.ld;
+    if constexpr (GS == 1) {
+        // one column: lane zl takes nonzeros zl, zl + NZL, zl + 2 NZL, ... (the order of the
+        // general loop below), loading U indices and keeping U gathers in flight per round
+        for (int64_t base = beg; base < end; base += (int64_t)NZL * U) {
+            int j[U];
+            T wu[U];
+            T x[U][VEC];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = base + (int64_t)u * NZL + zl;
+                j[u] = e < end ? __ldg(a.col + e) : -1;
+                if constexpr (WEIGHTED) wu[u] = e < end ? (T)__ldg(a.w + e) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j[u] >= 0) {
+                    ld_gather<T, VEC>(x[u], q + (int64_t)j[u] * ld);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) x[u][i] = T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    if constexpr (WEIGHTED) acc[i] += wu[u] * x[u][i];
+                    else acc[i] += x[u][i];
+                }
+            }
+        }
+        return;
+    }
     for (int64_t base = beg; base < end; base += G) {
         const int cnt = (int)(end - base < G ? end - base : G);
         const int my_col = li < cnt ? __ldg(a.col + base + li) : 0;
