@@ -901,6 +901,19 @@ __global__ void __launch_bounds__(kBlock) k_spmv_tasks(const StepArgs<T> a)
             continue;
         }
         const int cnt = (int)(e1 - e0);
+        // operands of each lane's first row in phase 2, loaded now so that their latency
+        // overlaps the gathers of phase 1
+        const int rf = r0 + lane;
+        int fb0 = 0, fb1 = 0;
+        T fqp = T(0), fqc = T(0), finvd = T(0), fdu = T(0);
+        if (rf < r1) {
+            fb0 = (int)(a.row_ptr[rf] - e0);
+            fb1 = (int)(a.row_ptr[rf + 1] - e0);
+            fqp = a.qprev_w[rf];
+            fqc = a.qcur[rf];
+            finvd = a.invdeg[rf];
+            fdu = a.deg[rf];
+        }
         // phase 1: products into shared memory
         for (int k0 = 0; k0 < cnt; k0 += 32 * 8) {
             T x[8];
@@ -926,15 +939,19 @@ __global__ void __launch_bounds__(kBlock) k_spmv_tasks(const StepArgs<T> a)
         }
         __syncwarp();
         // phase 2: one lane per row
-        for (int r = r0 + lane; r < r1; r += 32) {
-            const int b0 = (int)(a.row_ptr[r] - e0), b1 = (int)(a.row_ptr[r + 1] - e0);
+        for (int r = rf; r < r1; r += 32) {
+            const bool first = r == rf;
+            const int b0 = first ? fb0 : (int)(a.row_ptr[r] - e0);
+            const int b1 = first ? fb1 : (int)(a.row_ptr[r + 1] - e0);
             T sum = T(0);
             for (int k = b0; k < b1; ++k) sum += pw[k];
             T acc[1] = {sum}, qp[1], qc[1], bt1[1] = {bt};
-            qp[0] = a.qprev_w[r];
-            qc[0] = a.qcur[r];
+            qp[0] = first ? fqp : a.qprev_w[r];
+            qc[0] = first ? fqc : a.qcur[r];
+            const T invd = first ? finvd : a.invdeg[r];
+            const T du = first ? fdu : a.deg[r];
             Acc<T> tA[1] = {sA}, tB[1] = {sB}, tC[1] = {sC};
-            row_epilogue<T, 1>(a, r, 0, a.invdeg[r], a.deg[r], acc, bt1, qp, qc, tA, tB, tC);
+            row_epilogue<T, 1>(a, r, 0, invd, du, acc, bt1, qp, qc, tA, tB, tC);
             sA = tA[0];
             sB = tB[0];
             sC = tC[0];
