@@ -53,3 +53,29 @@ def test_two_gloo_ranks_shard_pairs_and_take_max_time():
     assert m0 == m1 == 150.0                       # both ranks see the slowest rank's time
     assert v0 == v1 == pytest.approx(16 * 2 * 10 / 0.150)
     assert (s0, t0) != (s1, t1)                    # different pairs on each rank
+
+
+def test_reference_arm_prints_one_json_line():
+    """bench.py --impl reference times the CPU oracle on a bounded sample of the bench
+    workload and prints one JSON line with the contract's keys (runs on CPU, no GPU)."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", "--ref-sample", "2"], capture_output=True, text=True, env=env,
+                         timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
