@@ -172,12 +172,12 @@ def workload(rank: int, n: int = 1_000_000, pairs: int = 256):
     return g, s, t
 
 
-def cpu_oracle(g, s, t, sample: int):
+def cpu_oracle(g, s, t, sample: int, threads: int = 0):
     from oracle import lanczos as O
 
     O.build()
     t0 = time.perf_counter()
-    r, k, used = O.lanczos_batch(g, s[:sample], t[:sample], k_max=K_MAX, stop_tol=1e-9, threads=0)
+    r, k, used = O.lanczos_batch(g, s[:sample], t[:sample], k_max=K_MAX, stop_tol=1e-9, threads=threads)
     dt = time.perf_counter() - t0
     return r, k, used, dt
 
@@ -399,6 +399,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--plain-sample", type=int, default=16)
+    ap.add_argument("--cpu1-sample", type=int, default=8, help="pairs of the one-core oracle timing")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -553,6 +554,10 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
         if plain_r is not None:
             ps = plain_r.size
             cpu["max_rel_err_plain_vs_oracle"] = float((np.abs(plain_r - r_or[:ps]) / np.abs(r_or[:ps])).max())
+        # one core (the paper's setting: one CPU thread), on a smaller sample of the same pairs
+        _, _, _, dt1 = cpu_oracle(g, s_np, t_np, args.cpu1_sample, threads=1)
+        cpu["single_core"] = {"value": args.cpu1_sample / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{args.cpu1_sample} of the {P} pairs"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
