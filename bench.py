@@ -217,11 +217,12 @@ def run_config_sweep(rd, timed):
                     residual 1e-10; error against the dense pseudo-inverse;
     chunglu1m    -- 256 pairs, FP32 vectors, rel_tol 1e-6: batched vs plain (16 pairs) pairs/s;
                     error against the FP64 oracle on 32 sampled pairs;
-    roadgrid4096 -- 64 pairs, FP64, rel_tol 1e-6 (the FP32-vector floor at this condition number is
-                    about 5e-5, so FP32 runs to relative residual 1e-6 for time only); error of 4
-                    pairs against the same pairs run to relative residual 1e-10;
-    chunglu4m_w  -- 32 pairs, gradient over all edges (rd_edge_grad, FP32 vectors), gradients/s
-                    and the forward error against the oracle on 4 pairs;
+    roadgrid4096 -- 64 pairs, double-float vectors (FP64-class), rel_tol 1e-6 (the FP32-vector floor
+                    at this condition number is about 5e-5, so FP32 runs to relative residual 1e-6
+                    for time only); error of 4 pairs against the same pairs run to relative
+                    residual 1e-10;
+    chunglu4m_w  -- 32 pairs, gradient over all edges (rd_edge_grad, FP32 vectors, device in and
+                    out), gradients/s and the forward error against the oracle on 4 pairs;
     rmat24       -- 128 pairs, FP32 vectors, rel_tol 1e-6: batched vs plain (8 pairs) pairs/s;
                     error against the oracle on 8 sampled pairs."""
     import torch
@@ -266,13 +267,13 @@ def run_config_sweep(rd, timed):
 
     g, s, t = W.roadgrid4096()
     G = rd.Graph.from_csr(g)
-    ms64, r64 = timed(lambda: G.query(s, t, mode="fp64", k_max=40000, rel_tol=1e-6), reps=1)
+    msdf, rdf = timed(lambda: G.query(s, t, mode="df64", k_max=40000, rel_tol=1e-6), reps=1)
     ms32, r32 = timed(lambda: G.query(s, t, mode="fp32", k_max=40000, rel_tol=0.0, resid_tol=1e-6), reps=1)
-    tight = G.query(s[:4], t[:4], mode="fp64", k_max=60000, rel_tol=0.0, resid_tol=1e-10)
+    tight = G.query(s[:4], t[:4], mode="df64", k_max=60000, rel_tol=0.0, resid_tol=1e-10)
     line(workload="roadgrid4096", n=g.n, nnz=g.nnz, pairs=len(s),
-         fp64_rel_tol_1e6={"query_ms": ms64, "pairs_per_s": len(s) / (ms64 / 1e3),
-                           "iters_median": float(np.median(r64.iters)), "iters_max": int(r64.iters.max()),
-                           "max_rel_err_vs_resid1e-10": rel(r64.r[:4], tight.r)},
+         df64_rel_tol_1e6={"query_ms": msdf, "pairs_per_s": len(s) / (msdf / 1e3),
+                           "iters_median": float(np.median(rdf.iters)), "iters_max": int(rdf.iters.max()),
+                           "max_rel_err_vs_resid1e-10": rel(rdf.r[:4], tight.r)},
          fp32_resid_1e6={"query_ms": ms32, "pairs_per_s": len(s) / (ms32 / 1e3),
                          "iters_median": float(np.median(r32.iters)), "iters_max": int(r32.iters.max()),
                          "max_rel_err_vs_resid1e-10": rel(r32.r[:4], tight.r)},
@@ -281,15 +282,17 @@ def run_config_sweep(rd, timed):
 
     g, s, t = W.chunglu4m_w()
     G = rd.Graph.from_csr(g)
-    ones = np.ones(len(s))
-    ms_g, (gw, r) = timed(lambda: G.edge_grad(s, t, ones, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
-    ms_f, rf = timed(lambda: G.query(s, t, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
+    sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
+    ones = torch.ones(len(s), dtype=torch.float64, device="cuda")
+    # device in, device out: the gradient (one float per stored entry) stays in HBM
+    ms_g, (gw, r) = timed(lambda: G.edge_grad(sd, td, ones, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
+    ms_f, rf = timed(lambda: G.query(sd, td, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
     idx = np.array([0, 9, 21, 30])
     ref, _, _ = O.lanczos_batch(g, s[idx], t[idx], k_max=200, stop_tol=1e-13, threads=0)
     line(workload="chunglu4m_w", n=g.n, nnz=g.nnz, pairs=len(s), mode="fp32",
          gradient_ms=ms_g, gradients_per_s=len(s) / (ms_g / 1e3), forward_ms=ms_f,
-         gradient_over_forward=ms_g / ms_f, max_rel_err_r=rel(np.asarray(r)[idx], ref),
-         grad_entries=int(gw.size))
+         gradient_over_forward=ms_g / ms_f, max_rel_err_r=rel(r.cpu().numpy()[idx], ref),
+         grad_entries=int(gw.numel()))
     G.close()
 
 
