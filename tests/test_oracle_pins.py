@@ -306,3 +306,45 @@ def test_power_method_first_terms_by_hand():
     h = power.power_method(F.path(3), 0, 2, 2)
     assert h[0] == pytest.approx(1.0, abs=1e-15)
     assert h[1] == pytest.approx(1.5, abs=1e-15)
+
+
+def _laplacian_cg_r(g, s, t):
+    """r(s,t) from an independent solver: Jacobi-preconditioned conjugate gradients (scipy)
+    on L phi = e_s - e_t (consistent: the right-hand side sums to zero), r = phi_s - phi_t."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import LinearOperator, cg
+
+    w = np.ones(g.nnz) if g.w is None else g.w.astype(np.float64)
+    A = sp.csr_matrix((w, g.col, g.row_ptr), shape=(g.n, g.n))
+    d = np.asarray(A.sum(axis=1)).ravel()
+    L = sp.diags(d) - A
+    b = np.zeros(g.n)
+    b[s] += 1.0
+    b[t] -= 1.0
+    M = LinearOperator((g.n, g.n), matvec=lambda x: x / d)
+    try:
+        phi, info = cg(L, b, rtol=1e-14, atol=0.0, maxiter=200000, M=M)
+    except TypeError:  # older scipy spells the tolerance `tol`
+        phi, info = cg(L, b, tol=1e-14, atol=0.0, maxiter=200000, M=M)
+    assert info == 0
+    return phi[s] - phi[t]
+
+
+@pytest.mark.parametrize("family", ["chunglu", "grid_weighted", "ba"])
+def test_lanczos_vs_independent_cg_at_scale(family):
+    """Sizes where the dense pseudo-inverse is out of reach: the FP64 Lanczos oracle, run to a
+    1e-15 relative increment, agrees with Jacobi-CG on the Laplacian to 1e-9 relative."""
+    from graphgen import workloads as W
+
+    if family == "chunglu":
+        g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 4, 19)
+    elif family == "grid_weighted":
+        g = F.grid_deleted(90, 0.05, 4)
+        s, t = F.random_pairs(g.n, 4, 6)
+    else:
+        g = F.barabasi_albert(15000, 3, 8)
+        s, t = F.random_pairs(g.n, 4, 7)
+    for a, b in zip(s, t):
+        r_lz = lanczos.lanczos_pair(g, int(a), int(b), k_max=20000, stop_tol=1e-15)["r"]
+        r_cg = _laplacian_cg_r(g, int(a), int(b))
+        assert abs(r_lz - r_cg) / r_cg < 1e-9, (family, a, b, r_lz, r_cg)
