@@ -73,3 +73,36 @@ def test_package_has_no_cpu_fallback(monkeypatch, tmp_path):
             if f.endswith(".py"):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt
+
+
+def _header_struct_fields(name):
+    """(type, field) pairs of `typedef struct { ... } name;` in include/rd.h, in order."""
+    import re
+
+    text = open(os.path.join(ROOT, "include", "rd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    end = re.search(r"\}\s*" + name + r"\s*;", text)
+    assert end, name
+    start = text.rfind("typedef struct", 0, end.start())
+    body = text[text.index("{", start) + 1:end.start()]
+    out = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        typ, *names = decl.replace(",", " ").split()
+        out.extend((typ, n) for n in names)
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("rd_query_opts", "QueryOpts"), ("rd_call_stats", "CallStats")])
+def test_ctypes_structs_match_header(cname, pyname):
+    """The binding's ctypes mirrors of the ABI structs have the header's fields, order and types."""
+    from paper_2601_11159_gb300 import _lib
+
+    ctype = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double, "uint32_t": C.c_uint32}
+    hdr = _header_struct_fields(cname)
+    py = getattr(_lib, pyname)._fields_
+    assert [n for _, n in hdr] == [n for n, _ in py]
+    for (t, n), (_, pt) in zip(hdr, py):
+        assert ctype[t] == pt, (cname, n, t, pt)
