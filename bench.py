@@ -211,8 +211,37 @@ def run_reference(args, world, rank):
     return 0
 
 
-def run_config_sweep(rd, timed):
-    """One JSON line per synthetic workload (sizes and recipes in graphgen/workloads.py):
+def profile_config(rd, name):
+    """One SpMM-heavy query of a workload inside cudaProfilerStart/Stop, after a warm-up query
+    (which also runs the autotuner), for ncu --profile-from-start off: 4 fixed Lanczos steps
+    over all of the workload's pairs (double-float vectors for the road grid)."""
+    import torch
+
+    from graphgen import workloads as W
+
+    make = {"chunglu1m": W.chunglu1m, "rmat24": W.rmat24, "roadgrid4096": W.roadgrid4096,
+            "chunglu4m_w": W.chunglu4m_w, "grid64": W.grid64}[name]
+    g, s, t = make()
+    G = rd.Graph.from_csr(g)
+    sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
+    mode = "df64" if name == "roadgrid4096" else "fp32"
+    kw = dict(mode=mode, k_max=4, fixed_k=True)
+    G.query(sd, td, **kw)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    G.query(sd, td, **kw)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    st = G.last_stats()
+    print(json.dumps({"profiled": name, "mode": mode, "n": g.n, "nnz": g.nnz, "pairs": len(s),
+                      "rhs_tile": st["rhs_tile"], "kernel": st["kernel"], "spmm_bytes_per_launch":
+                      st["spmm_bytes"] / max(st["spmm_launches"], 1)}), flush=True)
+    G.close()
+
+
+def run_config_sweep(rd, timed, only=None):
+    """One JSON line per synthetic workload (sizes and recipes in graphgen/workloads.py), or only
+    the one named by `only`:
     grid64       -- one pair (corner to corner), FP64, plain single-vector path, stop at relative
                     residual 1e-10; error against the dense pseudo-inverse;
     chunglu1m    -- 256 pairs, FP32 vectors, rel_tol 1e-6: batched vs plain (16 pairs) pairs/s;
@@ -231,21 +260,27 @@ def run_config_sweep(rd, timed):
     from oracle import dense
     from oracle import lanczos as O
 
+    def want(name):
+        return only is None or only == name
+
     def line(**kw):
         print(json.dumps(dict(sweep="configs", **kw)), flush=True)
 
     def rel(a, b):
         return float(np.max(np.abs(np.asarray(a, np.float64) / np.asarray(b, np.float64) - 1)))
 
-    g, s, t = W.grid64()
-    G = rd.Graph.from_csr(g)
-    exact = dense.DenseRD.of(g).r(s, t)
-    ms, res = timed(lambda: G.query(s, t, mode="fp64", k_max=500, rel_tol=0.0, resid_tol=1e-10, plain=True))
-    line(workload="grid64", pairs=1, mode="fp64", path="plain", query_ms=ms, pairs_per_s=1e3 / ms,
-         iters=int(res.iters[0]), max_rel_err=rel(res.r, exact))
-    G.close()
+    if want("grid64"):
+        g, s, t = W.grid64()
+        G = rd.Graph.from_csr(g)
+        exact = dense.DenseRD.of(g).r(s, t)
+        ms, res = timed(lambda: G.query(s, t, mode="fp64", k_max=500, rel_tol=0.0, resid_tol=1e-10, plain=True))
+        line(workload="grid64", pairs=1, mode="fp64", path="plain", query_ms=ms, pairs_per_s=1e3 / ms,
+             iters=int(res.iters[0]), max_rel_err=rel(res.r, exact))
+        G.close()
 
     for name, make, pairs_plain in [("chunglu1m", W.chunglu1m, 16), ("rmat24", W.rmat24, 8)]:
+        if not want(name):
+            continue
         g, s, t = make()
         G = rd.Graph.from_csr(g)
         sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
@@ -265,38 +300,40 @@ def run_config_sweep(rd, timed):
              sampled_pairs=len(idx))
         G.close()
 
-    g, s, t = W.roadgrid4096()
-    G = rd.Graph.from_csr(g)
-    msdf, rdf = timed(lambda: G.query(s, t, mode="df64", k_max=40000, rel_tol=1e-6), reps=1)
-    ms32, r32 = timed(lambda: G.query(s, t, mode="fp32", k_max=40000, rel_tol=0.0, resid_tol=1e-6), reps=1)
-    tight = G.query(s[:4], t[:4], mode="df64", k_max=60000, rel_tol=0.0, resid_tol=1e-10)
-    line(workload="roadgrid4096", n=g.n, nnz=g.nnz, pairs=len(s),
-         df64_rel_tol_1e6={"query_ms": msdf, "pairs_per_s": len(s) / (msdf / 1e3),
-                           "iters_median": float(np.median(rdf.iters)), "iters_max": int(rdf.iters.max()),
-                           "max_rel_err_vs_resid1e-10": rel(rdf.r[:4], tight.r)},
-         fp32_resid_1e6={"query_ms": ms32, "pairs_per_s": len(s) / (ms32 / 1e3),
-                         "iters_median": float(np.median(r32.iters)), "iters_max": int(r32.iters.max()),
-                         "max_rel_err_vs_resid1e-10": rel(r32.r[:4], tight.r)},
-         reference_iters=tight.iters.tolist())
-    G.close()
+    if want("roadgrid4096"):
+        g, s, t = W.roadgrid4096()
+        G = rd.Graph.from_csr(g)
+        msdf, rdf = timed(lambda: G.query(s, t, mode="df64", k_max=40000, rel_tol=1e-6), reps=1)
+        ms32, r32 = timed(lambda: G.query(s, t, mode="fp32", k_max=40000, rel_tol=0.0, resid_tol=1e-6), reps=1)
+        tight = G.query(s[:4], t[:4], mode="df64", k_max=60000, rel_tol=0.0, resid_tol=1e-10)
+        line(workload="roadgrid4096", n=g.n, nnz=g.nnz, pairs=len(s),
+             df64_rel_tol_1e6={"query_ms": msdf, "pairs_per_s": len(s) / (msdf / 1e3),
+                               "iters_median": float(np.median(rdf.iters)), "iters_max": int(rdf.iters.max()),
+                               "max_rel_err_vs_resid1e-10": rel(rdf.r[:4], tight.r)},
+             fp32_resid_1e6={"query_ms": ms32, "pairs_per_s": len(s) / (ms32 / 1e3),
+                             "iters_median": float(np.median(r32.iters)), "iters_max": int(r32.iters.max()),
+                             "max_rel_err_vs_resid1e-10": rel(r32.r[:4], tight.r)},
+             reference_iters=tight.iters.tolist())
+        G.close()
 
-    g, s, t = W.chunglu4m_w()
-    G = rd.Graph.from_csr(g)
-    sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
-    ones = torch.ones(len(s), dtype=torch.float64, device="cuda")
-    # device in, device out: the gradient (one float per stored entry) stays in HBM
-    ms_g, (gw, r) = timed(lambda: G.edge_grad(sd, td, ones, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
-    ms_f, rf = timed(lambda: G.query(sd, td, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
-    idx = np.array([0, 9, 21, 30])
-    ref, _, _ = O.lanczos_batch(g, s[idx], t[idx], k_max=200, stop_tol=1e-13, threads=0)
-    line(workload="chunglu4m_w", n=g.n, nnz=g.nnz, pairs=len(s), mode="fp32",
-         gradient_ms=ms_g, gradients_per_s=len(s) / (ms_g / 1e3), forward_ms=ms_f,
-         gradient_over_forward=ms_g / ms_f, max_rel_err_r=rel(r.cpu().numpy()[idx], ref),
-         grad_entries=int(gw.numel()))
-    G.close()
+    if want("chunglu4m_w"):
+        g, s, t = W.chunglu4m_w()
+        G = rd.Graph.from_csr(g)
+        sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
+        ones = torch.ones(len(s), dtype=torch.float64, device="cuda")
+        # device in, device out: the gradient (one float per stored entry) stays in HBM
+        ms_g, (gw, r) = timed(lambda: G.edge_grad(sd, td, ones, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
+        ms_f, rf = timed(lambda: G.query(sd, td, mode="fp32", k_max=200, rel_tol=1e-6), reps=2)
+        idx = np.array([0, 9, 21, 30])
+        ref, _, _ = O.lanczos_batch(g, s[idx], t[idx], k_max=200, stop_tol=1e-13, threads=0)
+        line(workload="chunglu4m_w", n=g.n, nnz=g.nnz, pairs=len(s), mode="fp32",
+             gradient_ms=ms_g, gradients_per_s=len(s) / (ms_g / 1e3), forward_ms=ms_f,
+             gradient_over_forward=ms_g / ms_f, max_rel_err_r=rel(r.cpu().numpy()[idx], ref),
+             grad_entries=int(gw.numel()))
+        G.close()
 
 
-def run_sweeps(which: str):
+def run_sweeps(which: str, only=None, profile=False):
     """Extra measurements beyond the main line (one JSON line each):
     scaling  -- Erdos-Renyi and Barabasi-Albert graphs, n = 1e2..1e6, m = n ln n, k = 20 fixed,
                 64 pairs, FP32 (the scalability experiment, Exp-3);
@@ -365,7 +402,10 @@ def run_sweeps(which: str):
                                       "max_abs_err": float(np.max(np.abs(r - exact)))}), flush=True)
             G.close()
     if which in ("configs", "all"):
-        run_config_sweep(rd, timed)
+        if profile:
+            profile_config(rd, only or "chunglu1m")
+        else:
+            run_config_sweep(rd, timed, only)
     if which in ("pm", "all"):
         from graphgen import workloads as W
 
@@ -412,11 +452,14 @@ def main():
     ap.add_argument("--rhs-tile", type=int, default=0)
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--only", default=None,
+                    choices=["grid64", "chunglu1m", "rmat24", "roadgrid4096", "chunglu4m_w"],
+                    help="with --sweep configs: one workload; with --profile-range: a short profiled query of it")
     ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "configs", "all"],
                     help="extra measurements instead of the main line")
     args = ap.parse_args()
     if args.sweep:
-        return run_sweeps(args.sweep)
+        return run_sweeps(args.sweep, args.only, args.profile_range)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()
