@@ -73,6 +73,48 @@ __device__ __forceinline__ df64& operator-=(df64& a, df64 b)
     return a;
 }
 
+// Accumulation of gathered terms into a running sum (the gather loops of the SpMM). For
+// float and double a plain multiply-add. For df64 the leading parts go through TwoSum and the
+// trailing parts are summed in FP32 without renormalising after every term (about 11 FP32
+// operations per weighted term instead of 17); acc_finish renormalises once per row.
+template <typename T>
+__device__ __forceinline__ void acc_mul_add(T& acc, T w, T x)
+{
+    acc += w * x;
+}
+template <typename T>
+__device__ __forceinline__ void acc_add(T& acc, T x)
+{
+    acc += x;
+}
+template <typename T>
+__device__ __forceinline__ void acc_finish(T&)
+{
+}
+template <>
+__device__ __forceinline__ void acc_mul_add<df64>(df64& acc, df64 w, df64 x)
+{
+    const float p = __fmul_rn(w.hi, x.hi);
+    float e = __fmaf_rn(w.hi, x.hi, -p);  // exact low part of w.hi * x.hi
+    e = __fmaf_rn(w.hi, x.lo, e);
+    e = __fmaf_rn(w.lo, x.hi, e);
+    const df64 s = df_two_sum(acc.hi, p);
+    acc.hi = s.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
+}
+template <>
+__device__ __forceinline__ void acc_add<df64>(df64& acc, df64 x)
+{
+    const df64 s = df_two_sum(acc.hi, x.hi);
+    acc.hi = s.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, x.lo));
+}
+template <>
+__device__ __forceinline__ void acc_finish<df64>(df64& acc)
+{
+    acc = df_two_sum(acc.hi, acc.lo);
+}
+
 // Warp shuffles of element values (both halves move together).
 __device__ __forceinline__ float shfl_xor_t(unsigned mask, float v, int off, int width = 32)
 {

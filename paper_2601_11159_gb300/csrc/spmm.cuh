@@ -257,11 +257,13 @@ __device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t beg, in
             for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) {
-                    if constexpr (WEIGHTED) acc[i] += wu[u] * x[u][i];
-                    else acc[i] += x[u][i];
+                    if constexpr (WEIGHTED) acc_mul_add(acc[i], wu[u], x[u][i]);
+                    else acc_add(acc[i], x[u][i]);
                 }
             }
         }
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc_finish(acc[i]);
         return;
     }
     for (int64_t base = beg; base < end; base += G) {
@@ -288,12 +290,14 @@ __device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t beg, in
             for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) {
-                    if constexpr (WEIGHTED) acc[i] += wu[u] * x[u][i];
-                    else acc[i] += x[u][i];
+                    if constexpr (WEIGHTED) acc_mul_add(acc[i], wu[u], x[u][i]);
+                    else acc_add(acc[i], x[u][i]);
                 }
             }
         }
     }
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) acc_finish(acc[i]);
 }
 
 template <int GS, int NZL, typename T, int VEC>
@@ -808,6 +812,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
                             const int wi = row - w0;
                             const T invd = shfl_t(mask, my_invd, wi, GS);
                             const T du = shfl_t(mask, my_deg, wi, GS);
+#pragma unroll
+                            for (int i = 0; i < VEC; ++i) acc_finish(acc[i]);
                             row_epilogue_b<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, rb, sacc);
 #pragma unroll
                             for (int i = 0; i < VEC; ++i) acc[i] = T(0);
@@ -824,10 +830,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
                         }
                         if constexpr (WEIGHTED) {
 #pragma unroll
-                            for (int i = 0; i < VEC; ++i) acc[i] += wu[u] * x[u][i];
+                            for (int i = 0; i < VEC; ++i) acc_mul_add(acc[i], wu[u], x[u][i]);
                         } else {
 #pragma unroll
-                            for (int i = 0; i < VEC; ++i) acc[i] += x[u][i];
+                            for (int i = 0; i < VEC; ++i) acc_add(acc[i], x[u][i]);
                         }
                     }
                 }
@@ -837,6 +843,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
                 const int wi = row - w0;
                 const T invd = shfl_t(mask, my_invd, wi, GS);
                 const T du = shfl_t(mask, my_deg, wi, GS);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) acc_finish(acc[i]);
                 row_epilogue_b<T, VEC>(a, row, c0, invd, du, acc, bt, qp, qc, rb, sacc);
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) acc[i] = T(0);
