@@ -52,14 +52,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def load_traffic(workload: str):
+def load_traffic(workload: str, launches_per_query: float):
     """DRAM bytes per SpMM launch from the committed ncu summary, if it was taken on the
-    current kernel source and on this workload (else None)."""
+    current kernel source, on this workload and over the same SpMM launches per query (the
+    mean is over that mix of widths), else None."""
     p = os.path.join(ROOT, "profiles", "spmm_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("kernel_source_sha1") != kernel_source_hash() or d.get("workload") != workload:
+        return None
+    if d.get("spmm_launches_per_query") != round(launches_per_query):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -584,7 +587,7 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
     avg_launch_ms = spmm_ms / max(spmm_n, 1)
     achieved = spmm_bytes / (spmm_ms / 1000.0) / 1e9 if spmm_n and spmm_ms > 0 else None
     workload_name = "chunglu1m_256pairs" if args.n == 1_000_000 and P == 256 else f"chunglu{args.n}_{P}pairs"
-    traffic = load_traffic(workload_name)
+    traffic = load_traffic(workload_name, spmm_n / max(args.steps, 1))
 
     cpu = None
     max_rel = None

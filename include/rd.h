@@ -92,8 +92,14 @@ typedef enum {
                                e_1^T (I-T_k)^{-1} e_1 (the error of the estimate 4 steps back)
                                instead of the default geometric tail estimate (see rel_tol) */
 #define RD_Q_NO_GRAPH 128u  /* rd_query: launch every kernel of every step from the host instead
-                               of replaying a captured CUDA graph of two steps (the results are
+                               of replaying a captured CUDA graph of one step (the results are
                                bitwise the same; RD_Q_PROFILE also turns the graphs off) */
+#define RD_Q_DENSE_FIRST 512u /* compute the first step's product D^{-1} A q_1 with the SpMM over
+                               every row. By default, when the graph's rows are sorted by column
+                               and its entries symmetric (checked by rd_graph_create and
+                               rd_graph_set_weights), a kernel visits only the rows adjacent to s
+                               and t, where q_1 (nonzero in rows s and t alone) makes it nonzero;
+                               the two agree to rounding */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */
@@ -136,6 +142,8 @@ typedef struct {
     int32_t compactions;     /* times the active pairs were packed into a narrower block */
     int32_t tuned;           /* 1 if the configuration came from the autotuner's table */
     int32_t row_order;       /* 1 if the row-group kernel visited rows by decreasing degree */
+    int32_t sparse_first;    /* 1 if the first step visited only the rows adjacent to s and t
+                                (see RD_Q_DENSE_FIRST) */
 } rd_call_stats;
 
 /* Fill `opts` with defaults: k_max 1000, rel_tol 1e-7, resid_tol 0, FP32 vectors with FP64

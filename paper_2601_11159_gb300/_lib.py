@@ -39,6 +39,7 @@ RD_Q_NO_ONCHIP = 32
 RD_Q_NO_TUNE = 64
 RD_Q_NO_GRAPH = 128
 RD_Q_EST_DELAYED = 256
+RD_Q_DENSE_FIRST = 512
 
 
 class QueryOpts(C.Structure):
@@ -70,6 +71,7 @@ class CallStats(C.Structure):
         ("compactions", C.c_int32),
         ("tuned", C.c_int32),
         ("row_order", C.c_int32),
+        ("sparse_first", C.c_int32),
     ]
 
 

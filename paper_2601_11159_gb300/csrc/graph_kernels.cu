@@ -35,6 +35,37 @@ __global__ void k_check_csr(int64_t n, int64_t nnz, const int64_t* rp, const int
     }
 }
 
+// Flags a CSR whose rows are not strictly increasing in column, or which is not symmetric
+// entry for entry (row v holds u with the same weight bits as row u holds v): the sparse
+// first Lanczos step reads row s's weights in place of row u's.
+__global__ void k_rows_not_sorted_symmetric(int64_t n, const int64_t* rp, const int32_t* col, const float* w,
+                                            int32_t* flag)
+{
+    // one warp per row, lanes over its entries
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += nwarps) {
+        const int64_t beg = rp[u], end = rp[u + 1];
+        bool bad = false;
+        for (int64_t e = beg + lane; e < end && !bad; e += 32) {
+            const int32_t v = col[e];
+            if (e > beg && v <= col[e - 1]) {
+                bad = true;
+                break;
+            }
+            const int64_t vend = rp[v + 1];
+            int64_t lo = rp[v], hi = vend;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (col[mid] < (int32_t)u) lo = mid + 1; else hi = mid;
+            }
+            bad = lo >= vend || col[lo] != (int32_t)u ||
+                  (w != nullptr && __float_as_uint(w[lo]) != __float_as_uint(w[e]));
+        }
+        if (bad) atomicOr(flag, 1);
+    }
+}
+
 // Self-loops need the row of each entry: one thread per row.
 __global__ void k_count_self_loops(int64_t n, const int64_t* rp, const int32_t* col, CheckFlags* f)
 {
@@ -84,6 +115,21 @@ static int grid_for(int64_t work, int sm)
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (int)g;
+}
+
+rd_status rows_sorted_symmetric(rd_graph* g, cudaStream_t st, bool* out)
+{
+    int32_t* f = nullptr;
+    RD_CUDA(cudaMallocAsync((void**)&f, sizeof(int32_t), st));
+    RD_CUDA(cudaMemsetAsync(f, 0, sizeof(int32_t), st));
+    if (g->n > 0)
+        k_rows_not_sorted_symmetric<<<grid_for(g->n, g->sm_count), 256, 0, st>>>(g->n, g->row_ptr, g->col, g->w, f);
+    int32_t h = 0;
+    RD_CUDA(cudaMemcpyAsync(&h, f, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RD_CUDA(cudaFreeAsync(f, st));
+    RD_CUDA(cudaStreamSynchronize(st));
+    *out = h == 0;
+    return RD_OK;
 }
 
 rd_status check_csr(rd_graph* g, cudaStream_t st, int64_t* self_loops)

@@ -313,6 +313,7 @@ static rd_status graph_build(rd_graph* g, const int64_t* row_ptr, const int32_t*
     RD_CUDA(cudaMalloc((void**)&g->invdeg32, sizeof(float) * n));
     RD_TRY(compute_degrees(g, st));
     RD_TRY(build_heavy(g, rp));
+    RD_TRY(rows_sorted_symmetric(g, st, &g->rows_sorted_sym));
     if (flags & RD_LABEL_COMPONENTS) {
         std::vector<int32_t> lab;
         g->ncomp = label_components(n, rp, col, lab);
@@ -601,7 +602,8 @@ struct RunCtx {
     bool in_region_x = false;
     bool lazy_walk = false;  // Power Method steps instead of Lanczos steps
     bool onchip = false;     // whole recurrence per pair in one CTA (small graphs, queries only)
-    bool graph = false;      // steps replayed from a captured CUDA graph of two steps
+    bool graph = false;      // steps replayed from a captured CUDA graph of one step
+    bool sparse_first = false;  // first step run by k_step0_sparse
     int compactions = 0;
     EventPool* ev = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
@@ -723,6 +725,42 @@ static void enqueue_normalize(RunCtx& c, int j, bool with_phi)
     a.coef = with_phi ? static_cast<const T*>(c.b.coef_hist) + (int64_t)j * c.cur.ld : nullptr;
     a.active_prev = with_phi ? nullptr : c.b.st.act_count + j;
     launch_normalize_t(c.cur.grid_norm, c.st, a);
+    ++c.launches;
+}
+
+// The first step's product from the sparse start vector (k_step0_sparse) instead of the
+// SpMM: for CSR with sorted, symmetric rows (checked once per graph and weight set).
+static bool sparse_first_step(const RunCtx& c)
+{
+    return c.g->rows_sorted_sym && !c.lazy_walk && (c.o.flags & RD_Q_DENSE_FIRST) == 0;
+}
+
+static void launch_step0_t(cudaStream_t st, const Step0Args<float>& a) { launch_step0_f32(st, a); }
+static void launch_step0_t(cudaStream_t st, const Step0Args<double>& a) { launch_step0_f64(st, a); }
+static void launch_step0_t(cudaStream_t st, const Step0Args<df64>& a) { launch_step0_df64(st, a); }
+
+template <typename T>
+static void enqueue_step0(RunCtx& c, bool reduce)
+{
+    const rd_graph* g = c.g;
+    Step0Args<T> a{};
+    a.n = g->n;
+    a.ld = c.cur.ld;
+    a.npairs = (int)c.P;
+    a.tp = c.cur.cfg.tp();
+    a.row_ptr = g->row_ptr;
+    a.col = g->col;
+    a.w = g->w;
+    if constexpr (std::is_same<T, df64>::value) a.invdeg = g->invdegdf;
+    else if constexpr (sizeof(T) == 8) a.invdeg = g->invdeg64;
+    else a.invdeg = g->invdeg32;
+    a.deg64 = g->deg64;
+    a.s = c.b.s;
+    a.t = c.b.t;
+    a.q1 = static_cast<const T*>(c.b.q[1]);
+    a.wout = static_cast<T*>(c.b.q[0]);
+    a.block_part = reduce ? c.b.block_part : nullptr;
+    launch_step0_t(c.st, a);
     ++c.launches;
 }
 
@@ -976,15 +1014,19 @@ static rd_status run_forward(RunCtx& c)
     if (c.lagged_polls)
         for (int i = 0; i < kSlots; ++i) poll_ev[i] = c.ev->get();
     int last_known = h[1];
+    const bool sparse0 = sparse_first_step(c);
+    c.sparse_first = sparse0;
     for (int j = 0; j < c.pl.k_max; ++j) {
-        if (c.graph) {
+        const bool sparse = j == 0 && sparse0;
+        if (c.graph && !sparse) {
             RD_TRY(launch_step_graph<T>(c, fa));
         } else {
-            RD_TRY(enqueue_spmm<T>(c, j, true));
+            if (sparse) enqueue_step0<T>(c, true);
+            else RD_TRY(enqueue_spmm<T>(c, j, true));
             fa.step = j;
             fa.ld = c.cur.ld;
             fa.tp = c.cur.cfg.tp();
-            fa.nblocks = c.cur.grid_main;
+            fa.nblocks = sparse ? 1 : c.cur.grid_main;
             if (c.compact) {
                 fa.slot_pair = c.slot_sel >= 0 ? c.b.slot_pair[c.slot_sel] : nullptr;
                 fa.cf_step = c.b.cf_cur[c.cf_sel];
@@ -997,6 +1039,10 @@ static rd_status run_forward(RunCtx& c)
             launch_finalize(c.st, fa);
             ++c.launches;
             enqueue_normalize<T>(c, j, false);
+            if (c.graph) {  // graph-replayed steps read the step index from device memory
+                launch_step_advance(c.st, c.b.step_dev, c.pl.k_max);
+                ++c.launches;
+            }
         }
         std::swap(c.b.q[0], c.b.q[1]);
         c.steps = j + 1;
@@ -1078,6 +1124,7 @@ static void record_stats(RunCtx& c)
     s.compactions += c.compactions;
     s.tuned = c.pl.tuned ? 1 : 0;
     s.row_order = c.pl.cfg.order;
+    s.sparse_first = c.sparse_first ? 1 : 0;
     if (c.profile) {
         double ms = 0.0;
         for (auto& pr : c.spmm_ev) {
@@ -1298,8 +1345,10 @@ static rd_status run_replay(RunCtx& c, int K)
     const int64_t vbytes = c.g->n * c.pl.ld * (int64_t)c.pl.elem;
     RD_CUDA(cudaMemsetAsync(c.b.phi, 0, vbytes, c.st));
     enqueue_init(c, true);
+    const bool sparse0 = sparse_first_step(c);
     for (int j = 0; j < K; ++j) {
-        RD_TRY(enqueue_spmm<T>(c, j, false));
+        if (j == 0 && sparse0) enqueue_step0<T>(c, false);
+        else RD_TRY(enqueue_spmm<T>(c, j, false));
         enqueue_normalize<T>(c, j, true);
         std::swap(c.b.q[0], c.b.q[1]);
     }
@@ -1448,7 +1497,8 @@ rd_status rd_graph_set_weights(rd_graph* g, const float* weights, void* stream)
     g->weighted = true;
     int64_t loops = 0;
     RD_TRY(check_csr(g, st, &loops));
-    return compute_degrees(g, st);
+    RD_TRY(compute_degrees(g, st));
+    return rows_sorted_symmetric(g, st, &g->rows_sorted_sym);
 }
 
 rd_status rd_graph_destroy(rd_graph* g)

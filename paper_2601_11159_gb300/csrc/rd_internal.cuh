@@ -265,6 +265,7 @@ struct rd_graph {
     int32_t* row_order = nullptr;
     // row of every stored entry (built on first use by the per-entry kernels)
     int32_t* entry_row = nullptr;
+    bool rows_sorted_sym = false;     // rows strictly increasing in column, entries symmetric
     double mean_deg = 0.0;
     rd::Workspace ws;
     rd_call_stats stats{};
@@ -361,8 +362,30 @@ void launch_edge_grad_f32(int grid, cudaStream_t st, const EdgeGradArgs<float>& 
 void launch_edge_grad_f64(int grid, cudaStream_t st, const EdgeGradArgs<double>& a);
 void launch_entry_rows(int grid, cudaStream_t st, int64_t n, const int64_t* row_ptr, int32_t* entry_row);
 
+// First Lanczos step from the sparse start vector (two nonzeros per column).
+template <typename T>
+struct Step0Args {
+    int64_t n, ld;
+    int npairs;
+    int tp;                       // column tile of the plan (layout of block_part)
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* w;               // nullable
+    const T* invdeg;
+    const double* deg64;
+    const int32_t* s;
+    const int32_t* t;
+    const T* q1;                  // q_1 block (n x ld)
+    T* wout;                      // W, written over the zeroed q_0 block
+    double* block_part;           // [slab][1][3][TP]: each column's sums as one block (nullable)
+};
+void launch_step0_f32(cudaStream_t st, const Step0Args<float>& a);
+void launch_step0_f64(cudaStream_t st, const Step0Args<double>& a);
+void launch_step0_df64(cudaStream_t st, const Step0Args<df64>& a);
+
 // Graph preparation kernels.
 rd_status graph_prepare(rd_graph* g, cudaStream_t st, uint32_t flags);
+rd_status rows_sorted_symmetric(rd_graph* g, cudaStream_t st, bool* out);
 rd_status graph_weights_changed(rd_graph* g, cudaStream_t st);
 
 }  // namespace rd

@@ -343,6 +343,127 @@ __global__ void k_step_advance(int32_t* step, int limit)
 
 void launch_step_advance(cudaStream_t st, int32_t* step, int limit) { k_step_advance<<<1, 1, 0, st>>>(step, limit); }
 
+// ------------------------------------------------------- sparse first step
+// q_1 is nonzero only in rows s and t of its column, so the first product
+// W = D^{-1} A q_1 (Algorithm 3 with q_0 = 0) is nonzero only on the rows adjacent to s or
+// t. One block per column: with L the endpoint of larger degree and S the other,
+//   pass 1, rows u in N(L):  W_u <- w_{uL} q_1[L]                       (partial row sum)
+//   pass 2, rows u in N(S):  u in N(L) (binary search in the sorted row L):
+//                              W_u <- W_u + w_{uS} q_1[S]                (still unscaled)
+//                            otherwise W_u <- (1/d_u) w_{uS} q_1[S]      (final)
+//   pass 3, rows u in N(L):  W_u <- (1/d_u) W_u                           (final)
+// and the column's sums A = sum d W q_1, B = sum d W^2, C = sum d W are taken in FP64 as one
+// block partial. Needs rows strictly increasing in column and symmetric entries (row u
+// holds L and S with the weights rows L and S hold u), so that these are the SpMM's rows.
+template <typename T>
+__device__ __forceinline__ void step0_term(T& acc, const float* w, int64_t e, T q)
+{
+    if (w) acc_mul_add(acc, T(__ldg(w + e)), q);
+    else acc_add(acc, q);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_step0_sparse(const Step0Args<T> a)
+{
+    __shared__ double red[8][3];
+    const int p = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t s = a.s[p], t = a.t[p];
+    bool live = s >= 0 && (int64_t)s < a.n && t >= 0 && (int64_t)t < a.n && s != t;
+    T q1s = T(0), q1t = T(0);
+    if (live) {
+        q1s = a.q1[(int64_t)s * a.ld + p];
+        q1t = a.q1[(int64_t)t * a.ld + p];
+        live = to_double(q1s) != 0.0 || to_double(q1t) != 0.0;
+    }
+    double* out = a.block_part ? a.block_part + (int64_t)(p / a.tp) * 3 * a.tp + p % a.tp : nullptr;
+    if (!live) {  // uniform over the block: the column stays zero
+        if (threadIdx.x == 0 && out) out[0] = out[a.tp] = out[2 * a.tp] = 0.0;
+        return;
+    }
+    const int64_t ds_n = a.row_ptr[s + 1] - a.row_ptr[s], dt_n = a.row_ptr[t + 1] - a.row_ptr[t];
+    const bool s_large = ds_n >= dt_n;
+    const int32_t L = s_large ? s : t, S = s_large ? t : s;
+    const T q1L = s_large ? q1s : q1t, q1S = s_large ? q1t : q1s;
+    const int64_t lb = a.row_ptr[L], le = a.row_ptr[L + 1];
+    const int64_t sb = a.row_ptr[S], se = a.row_ptr[S + 1];
+    const int64_t ld = a.ld;
+    double sA = 0.0, sB = 0.0, sC = 0.0;
+    auto add_sums = [&](int32_t u, T W) {
+        const double d = a.deg64[u], x = to_double(W);
+        sB += d * x * x;
+        sC += d * x;
+        if (u == s) sA += d * x * to_double(q1s);
+        else if (u == t) sA += d * x * to_double(q1t);
+    };
+    for (int64_t e = lb + threadIdx.x; e < le; e += blockDim.x) {
+        const int32_t u = __ldg(a.col + e);
+        T acc = T(0);
+        step0_term(acc, a.w, e, q1L);
+        acc_finish(acc);
+        a.wout[(int64_t)u * ld + p] = acc;
+    }
+    __syncthreads();
+    for (int64_t e = sb + threadIdx.x; e < se; e += blockDim.x) {
+        const int32_t u = __ldg(a.col + e);
+        int64_t lo = lb, hi = le;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(a.col + mid) < u) lo = mid + 1; else hi = mid;
+        }
+        T* wp = a.wout + (int64_t)u * ld + p;
+        if (lo < le && __ldg(a.col + lo) == u) {
+            T acc = *wp;
+            step0_term(acc, a.w, e, q1S);
+            acc_finish(acc);
+            *wp = acc;
+        } else {
+            T acc = T(0);
+            step0_term(acc, a.w, e, q1S);
+            acc_finish(acc);
+            const T W = a.invdeg[u] * acc;
+            *wp = W;
+            add_sums(u, W);
+        }
+    }
+    __syncthreads();
+    for (int64_t e = lb + threadIdx.x; e < le; e += blockDim.x) {
+        const int32_t u = __ldg(a.col + e);
+        T* wp = a.wout + (int64_t)u * ld + p;
+        const T W = a.invdeg[u] * *wp;
+        *wp = W;
+        add_sums(u, W);
+    }
+    if (!out) return;
+    // fixed-order reduction: xor tree within each warp, then warps in order
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        sA += __shfl_xor_sync(0xffffffffu, sA, off);
+        sB += __shfl_xor_sync(0xffffffffu, sB, off);
+        sC += __shfl_xor_sync(0xffffffffu, sC, off);
+    }
+    if (lane == 0) {
+        red[warp][0] = sA;
+        red[warp][1] = sB;
+        red[warp][2] = sC;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+        out[threadIdx.x * a.tp] = v;
+    }
+}
+
+template <typename T>
+static void launch_step0(cudaStream_t st, const Step0Args<T>& a)
+{
+    if (a.npairs > 0) k_step0_sparse<T><<<a.npairs, 256, 0, st>>>(a);
+}
+void launch_step0_f32(cudaStream_t st, const Step0Args<float>& a) { launch_step0<float>(st, a); }
+void launch_step0_f64(cudaStream_t st, const Step0Args<double>& a) { launch_step0<double>(st, a); }
+void launch_step0_df64(cudaStream_t st, const Step0Args<df64>& a) { launch_step0<df64>(st, a); }
+
 void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a) { launch_norm<float>(grid, st, a); }
 void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a) { launch_norm<double>(grid, st, a); }
 void launch_normalize_df64(int grid, cudaStream_t st, const NormArgs<df64>& a) { launch_norm<df64>(grid, st, a); }

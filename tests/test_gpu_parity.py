@@ -565,3 +565,64 @@ def test_double_float_mode_batched_chunglu(rd):
     gd, rd_ = G.edge_grad(s[:4], t[:4], None, mode="df64", k_max=300, rel_tol=0.0, resid_tol=1e-11)
     g6, r6 = G.edge_grad(s[:4], t[:4], None, mode="fp64", k_max=300, rel_tol=0.0, resid_tol=1e-11)
     assert np.array_equal(gd, g6) and np.array_equal(rd_, r6)
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-11), ("df64", 1e-11), ("fp32", 2e-5)])
+def test_sparse_first_step_matches_dense_first_step(rd, mode, tol):
+    """The first step computed from the sparse start vector (only the rows adjacent to s and
+    t) agrees with the SpMM over every row: fixed-k estimates and gradients, converged values
+    against the dense pseudo-inverse; on a power-law graph with hub endpoints (hub-hub pairs
+    share many neighbours), a grid with adjacent pairs and pairs whose endpoints share one or
+    two neighbours, and a weighted graph. Rows not sorted by column, or weights not symmetric
+    bit for bit, take the SpMM."""
+    cl, s_cl, t_cl = W.chunglu(20000, 2.1, 20.0, 200000, 24, 77)
+    hubs = np.argsort(np.diff(cl.row_ptr))[-3:].astype(np.int32)
+    s_cl = np.concatenate([s_cl, hubs, hubs[2:], t_cl[:1]]).astype(np.int32)
+    t_cl = np.concatenate([t_cl, np.roll(hubs, 1), s_cl[:1], hubs[:1]]).astype(np.int32)
+    grid = F.grid(20)
+    s_g = np.array([0, 21, 21, 0, 105, 399, 7], np.int32)
+    t_g = np.array([1, 42, 23, 399, 106, 398, 7], np.int32)
+    wg = F.random_connected(300, 900, 31, "lognormal")
+    s_w, t_w = F.random_pairs(wg.n, 12, 4)
+    for g, s, t in ((cl, s_cl, t_cl), (grid, s_g, t_g), (wg, s_w, t_w)):
+        G = rd.Graph.from_csr(g)
+        kw = dict(mode=mode, k_max=9, fixed_k=True, onchip=False)
+        a = G.query(s, t, **kw)
+        assert G.last_stats()["sparse_first"] == 1
+        b = G.query(s, t, sparse_first=False, **kw)
+        assert G.last_stats()["sparse_first"] == 0
+        nz = s != t
+        assert np.all(a.r[~nz] == 0.0) and np.array_equal(a.status, b.status)
+        assert rel(a.r[nz], b.r[nz]).max() < tol, (g.name, rel(a.r[nz], b.r[nz]).max())
+        ref = np.array([lanczos.lanczos_pair(g, int(x), int(y), k_max=9)["r"] if x != y else 0.0
+                        for x, y in zip(s, t)])
+        assert rel(a.r[nz], ref[nz]).max() < tol
+        conv = G.query(s, t, mode=mode, k_max=3000, rel_tol=0.0, resid_tol=1e-12 if mode != "fp32" else 1e-6)
+        assert np.all(conv.status == 0)
+        if g.n <= 400 or g is wg:
+            exact = dense.DenseRD.of(g).r(s[nz], t[nz])
+            assert rel(conv.r[nz], exact).max() < (FP64_TOL if mode != "fp32" else FP32_TOL)
+        if mode != "df64":
+            gk = dict(mode=mode, k_max=12, fixed_k=True)
+            ga, ra = G.edge_grad(s[nz][:8], t[nz][:8], None, **gk)
+            gb, rb = G.edge_grad(s[nz][:8], t[nz][:8], None, sparse_first=False, **gk)
+            assert rel(ra, rb).max() < tol
+            assert np.abs(ga - gb).max() <= 50 * tol * np.abs(gb).max()
+    # rows in decreasing column order
+    col = grid.col.copy()
+    for u in range(grid.n):
+        col[grid.row_ptr[u]:grid.row_ptr[u + 1]] = col[grid.row_ptr[u]:grid.row_ptr[u + 1]][::-1]
+    G2 = rd.Graph(grid.row_ptr, col, None)
+    r2 = G2.query(s_g, t_g, mode="fp64", k_max=3000, rel_tol=0.0, resid_tol=1e-12, onchip=False)
+    assert G2.last_stats()["sparse_first"] == 0
+    nz = s_g != t_g
+    assert rel(r2.r[nz], dense.DenseRD.of(grid).r(s_g[nz], t_g[nz])).max() < FP64_TOL
+    # one weight of one direction moved by one ulp
+    w = wg.w.copy()
+    w[0] = np.nextafter(w[0], np.float32(np.inf))
+    G3 = rd.Graph(wg.row_ptr, wg.col, w)
+    G3.query(s_w, t_w, mode="fp64", k_max=20, fixed_k=True, onchip=False)
+    assert G3.last_stats()["sparse_first"] == 0
+    G3.set_weights(wg.w)
+    G3.query(s_w, t_w, mode="fp64", k_max=20, fixed_k=True, onchip=False)
+    assert G3.last_stats()["sparse_first"] == 1
