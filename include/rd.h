@@ -100,6 +100,13 @@ typedef enum {
                                rd_graph_set_weights), a kernel visits only the rows adjacent to s
                                and t, where q_1 (nonzero in rows s and t alone) makes it nonzero;
                                the two agree to rounding */
+#define RD_Q_REPLAY_POTENTIAL 1024u /* rd_edge_grad / rd_potential / rd_flow: form the potential
+                               sum_j ||b|| z_j q_j (z = (I - T_k)^{-1} e_1) by a second pass that
+                               regenerates q_1..q_k from the stored coefficients (Algorithm 5),
+                               instead of the default direct update during the forward steps
+                               (p_i = q_i + (beta_i/delta_{i-1}) p_{i-1}, x += ||b|| (g_i/delta_i) p_i
+                               from the LDL^T factors of I - T_i; one extra vector, no second pass);
+                               the two agree to rounding */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */

@@ -40,6 +40,7 @@ RD_Q_NO_TUNE = 64
 RD_Q_NO_GRAPH = 128
 RD_Q_EST_DELAYED = 256
 RD_Q_DENSE_FIRST = 512
+RD_Q_REPLAY_POTENTIAL = 1024
 
 
 class QueryOpts(C.Structure):

@@ -490,6 +490,8 @@ struct Buffers {
     int32_t* step_dev;        // step index of graph-replayed steps (zeroed per query)
     // gradient / potential
     void* phi;
+    void* pvec;               // n x ld0: direction vectors of the potential's direct update
+    void* xcf;                // [k_max][2][ld0]: their coefficients (zeroed per query)
     void* coef_hist;
     void* gbar;
     double* zscratch;
@@ -543,6 +545,7 @@ static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, boo
     b->summary = c.take<int32_t>(2);
     b->err_flag = c.take<int32_t>(1);
     b->step_dev = c.take<int32_t>(1);
+    b->xcf = grad ? c.take<char>(K * 2 * ld * pl.elem) : nullptr;
     c.off = (c.off + 255) & ~size_t(255);
     b->state_bytes_end = c.off;
     b->s = c.take<int32_t>(P);
@@ -553,6 +556,7 @@ static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, boo
     b->status = c.take<int32_t>(P);
     if (grad) {
         b->phi = c.take<char>(n * ld * pl.elem);
+        b->pvec = c.take<char>(n * ld * pl.elem);
         b->coef_hist = c.take<char>(K * ld * pl.elem);
         b->gbar = c.take<char>(ld * pl.elem);
         b->zscratch = c.take<double>(K * 2 * ld);
@@ -604,6 +608,7 @@ struct RunCtx {
     bool onchip = false;     // whole recurrence per pair in one CTA (small graphs, queries only)
     bool graph = false;      // steps replayed from a captured CUDA graph of one step
     bool sparse_first = false;  // first step run by k_step0_sparse
+    bool pot_x = false;      // potential accumulated during the forward steps (k_normalize_pot)
     int compactions = 0;
     EventPool* ev = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
@@ -724,6 +729,11 @@ static void enqueue_normalize(RunCtx& c, int j, bool with_phi)
     a.phi = with_phi ? static_cast<T*>(c.b.phi) : nullptr;
     a.coef = with_phi ? static_cast<const T*>(c.b.coef_hist) + (int64_t)j * c.cur.ld : nullptr;
     a.active_prev = with_phi ? nullptr : c.b.st.act_count + j;
+    if (c.pot_x && !with_phi) {
+        a.pvec = static_cast<T*>(c.b.pvec);
+        a.xvec = static_cast<T*>(c.b.phi);
+        a.xcf = static_cast<const T*>(c.b.xcf) + (int64_t)j * 2 * c.cur.ld;
+    }
     launch_normalize_t(c.cur.grid_norm, c.st, a);
     ++c.launches;
 }
@@ -886,6 +896,12 @@ static void graph_step_args(RunCtx& c, const FinArgs& base, StepArgs<T>* sa, Fin
     na->step_dev = c.b.step_dev;
     na->cf_stride = stride;
     na->act_count = c.b.st.act_count;
+    if (c.pot_x) {
+        na->pvec = static_cast<T*>(c.b.pvec);
+        na->xvec = static_cast<T*>(c.b.phi);
+        na->xcf = static_cast<const T*>(c.b.xcf);
+        na->xcf_stride = 2 * ld;
+    }
 }
 
 // Launch one step from the graph cache (capturing and instantiating it on a miss).
@@ -973,6 +989,7 @@ static rd_status run_forward(RunCtx& c)
     fa.block_part = c.b.block_part;
     fa.st = c.b.st;
     fa.elem_size = (int)c.pl.elem;
+    fa.xcf = c.pot_x ? c.b.xcf : nullptr;
     int* h = c.g->h_pinned;
     // first poll: ids valid and at least one active pair
     RD_CUDA(cudaMemcpyAsync(h, c.b.err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
@@ -1360,6 +1377,14 @@ static rd_status forward_and_potential(RunCtx& c, const int32_t* s, const int32_
                                        rd_status* call_status)
 {
     RD_TRY(stage_pairs(c, s, t));
+    // the potential: accumulated during the forward steps (direct update), or, with
+    // RD_Q_REPLAY_POTENTIAL, by a second pass that regenerates the vectors
+    c.pot_x = (c.o.flags & RD_Q_REPLAY_POTENTIAL) == 0;
+    if (c.pot_x) {
+        const int64_t vbytes = c.g->n * c.pl.ld * (int64_t)c.pl.elem;
+        RD_CUDA(cudaMemsetAsync(c.b.phi, 0, vbytes, c.st));
+        RD_CUDA(cudaMemsetAsync(c.b.pvec, 0, vbytes, c.st));
+    }
     rd_status rs = c.pl.fp64 ? run_forward<double>(c) : run_forward<float>(c);
     if (rs < 0) return rs;
     // z-solve and gbar; a host grad_r is staged in the output buffer (free until the end)
@@ -1384,14 +1409,16 @@ static rd_status forward_and_potential(RunCtx& c, const int32_t* s, const int32_
     za.grad_r = d_grad;
     launch_zsolve(c.st, za);
     ++c.launches;
-    // K = max steps over pairs
-    std::vector<int32_t> ks(c.P);
-    RD_CUDA(cudaMemcpyAsync(ks.data(), c.b.st.k, sizeof(int32_t) * c.P, cudaMemcpyDeviceToHost, c.st));
-    RD_CUDA(cudaStreamSynchronize(c.st));
-    int K = 0;
-    for (int32_t k : ks) K = std::max(K, (int)k);
-    rs = c.pl.fp64 ? run_replay<double>(c, K) : run_replay<float>(c, K);
-    if (rs < 0) return rs;
+    if (!c.pot_x) {
+        // K = max steps over pairs
+        std::vector<int32_t> ks(c.P);
+        RD_CUDA(cudaMemcpyAsync(ks.data(), c.b.st.k, sizeof(int32_t) * c.P, cudaMemcpyDeviceToHost, c.st));
+        RD_CUDA(cudaStreamSynchronize(c.st));
+        int K = 0;
+        for (int32_t k : ks) K = std::max(K, (int)k);
+        rs = c.pl.fp64 ? run_replay<double>(c, K) : run_replay<float>(c, K);
+        if (rs < 0) return rs;
+    }
     *call_status = RD_OK;
     return RD_OK;
 }

@@ -128,6 +128,11 @@ struct NormArgs {
     const int32_t* step_dev;       // as StepArgs: cf + j * cf_stride, act_count[j]
     int64_t cf_stride;
     const int32_t* act_count;
+    // potential accumulated during the forward pass (nullable pvec: off)
+    T* pvec;                       // p_{i-1} in, p_i out
+    T* xvec;                       // x += mu_i p_i
+    const T* xcf;                  // [2][ld]: lambda_i, mu_i (+ j * xcf_stride with step_dev)
+    int64_t xcf_stride;
 };
 
 // Per-pair FP64 state of the running LDL^T factorisation of I - T_k.
@@ -165,6 +170,8 @@ struct FinArgs {
     const int32_t* step_dev;            // nullable: step index from device memory (graph replay);
     int64_t cf_stride;                  // then cf_step/cf_next advance by j * cf_stride
     int df;                             // 1: coefficients are stored as double-float pairs
+    void* xcf;                          // nullable T [k_max][2][ld]: step j receives lambda_i, mu_i
+                                        // of the potential's direct update (identity slot map only)
 };
 
 // Whole recurrence of one pair per CTA with q_{i-1}, q_i and W in shared memory (graphs

@@ -239,8 +239,16 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs a)
     const int64_t cfo = a.step_dev ? (int64_t)j * a.cf_stride : 0;
     T* cfs = static_cast<T*>(a.cf_step) + cfo;
     T* cfn = static_cast<T*>(a.cf_next) + cfo;
+    // factors of the previous step, for the potential's direct update below
+    const double lam = j > 0 ? st.beta[p] / st.delta[p] : 0.0;
     double alpha, cdef, beta_next;
     const bool stop = pair_update(a, st, p, j, A, B, C, &alpha, &cdef, &beta_next);
+    if (a.xcf && st.status[p] != RD_ERR_NUMERIC) {
+        // p_i = q_i + lambda_i p_{i-1}, x += mu_i p_i (a stopping step still contributes)
+        T* xc = static_cast<T*>(a.xcf) + (int64_t)j * 2 * ld;
+        xc[col] = (T)lam;
+        xc[ld + col] = (T)(sqrt(st.b2[p]) * st.g[p] / st.delta[p]);
+    }
     if (stop) {
         // zero coefficients: the column's vectors become (and stay) zero
         cfs[1 * ld + col] = T(0);
@@ -329,11 +337,67 @@ __global__ void __launch_bounds__(256) k_normalize(const NormArgs<T> a)
     }
 }
 
+// q_{i+1} as k_normalize, with the potential of each pair accumulated on the fly: the direct
+// form of the Lanczos solve (D-Lanczos, Saad, Iterative Methods for Sparse Linear Systems,
+// Section 6.7.1). With I - T_i = L D L^T (unit lower bidiagonal L, L[i][i-1] = -beta_i/delta_{i-1};
+// D = diag(delta)) and g = L^{-1} e_1, the vectors P = Q L^{-T} obey p_i = q_i + lambda_i p_{i-1},
+// lambda_i = beta_i/delta_{i-1}, and x_i = ||b|| Q_i (I - T_i)^{-1} e_1 = x_{i-1} + mu_i p_i with
+// mu_i = ||b|| g_i/delta_i: after the last step x is the potential of the replay pass
+// (sum_j ||b|| z_j q_j, z = (I - T_k)^{-1} e_1), without a second pass over the steps.
+template <typename T, bool VECD>
+__global__ void __launch_bounds__(256) k_normalize_pot(const NormArgs<T> a)
+{
+    const int32_t* act = a.step_dev ? a.act_count + *a.step_dev : a.active_prev;
+    if (act && *act == 0) return;
+    const int64_t j = a.step_dev ? *a.step_dev : 0;
+    const int64_t ld = a.ld;
+    const T* cfb = a.cf + j * a.cf_stride;
+    const T* xcb = a.xcf + j * a.xcf_stride;
+    const T* cf_al = cfb + ld;
+    const T* cf_c = cfb + 2 * ld;
+    const T* cf_ib = cfb + 3 * ld;
+    const T* cf_lam = xcb;
+    const T* cf_mu = xcb + ld;
+    constexpr int V = VECD ? 16 / (int)sizeof(T) : 1;
+    const int64_t units = a.n * ld / V;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += stride) {
+        const int64_t e0 = u * V, c0 = e0 % ld;
+        T w[V], qc[V], pv[V], xv[V], al[V], c[V], ib[V], lam[V], mu[V];
+        ld_stream<T, V>(w, a.w_to_qnext + e0);
+        ld_stream<T, V>(qc, a.qcur + e0);
+        ld_plain<T, V>(pv, a.pvec + e0);
+        ld_plain<T, V>(xv, a.xvec + e0);
+        ld_plain<T, V>(al, cf_al + c0);
+        ld_plain<T, V>(c, cf_c + c0);
+        ld_plain<T, V>(ib, cf_ib + c0);
+        ld_plain<T, V>(lam, cf_lam + c0);
+        ld_plain<T, V>(mu, cf_mu + c0);
+        T qn[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            qn[i] = (w[i] - al[i] * qc[i] - c[i]) * ib[i];
+            pv[i] = qc[i] + lam[i] * pv[i];
+            xv[i] += mu[i] * pv[i];
+        }
+        st_plain<T, V>(a.pvec + e0, pv);
+        st_plain<T, V>(a.xvec + e0, xv);
+        st_plain<T, V>(a.w_to_qnext + e0, qn);
+    }
+}
+
 template <typename T>
 static void launch_norm(int grid, cudaStream_t st, const NormArgs<T>& a)
 {
-    if (a.ld == 1) k_normalize<T, true><<<grid, 256, 0, st>>>(a);
-    else k_normalize<T, false><<<grid, 256, 0, st>>>(a);
+    constexpr int V = 16 / (int)sizeof(T);
+    if (a.pvec) {
+        if (a.ld % V == 0) k_normalize_pot<T, true><<<grid, 256, 0, st>>>(a);
+        else k_normalize_pot<T, false><<<grid, 256, 0, st>>>(a);
+    } else if (a.ld == 1) {
+        k_normalize<T, true><<<grid, 256, 0, st>>>(a);
+    } else {
+        k_normalize<T, false><<<grid, 256, 0, st>>>(a);
+    }
 }
 
 __global__ void k_step_advance(int32_t* step, int limit)

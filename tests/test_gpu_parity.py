@@ -626,3 +626,31 @@ def test_sparse_first_step_matches_dense_first_step(rd, mode, tol):
     G3.set_weights(wg.w)
     G3.query(s_w, t_w, mode="fp64", k_max=20, fixed_k=True, onchip=False)
     assert G3.last_stats()["sparse_first"] == 1
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-9), ("fp32", 3e-4)])
+def test_direct_potential_matches_replay_pass(rd, mode, tol):
+    """The potential accumulated during the forward steps (p_i = q_i + lambda_i p_{i-1},
+    x += mu_i p_i from the LDL^T factors of I - T_i) equals the replay pass's sum of
+    ||b|| z_j q_j: gradients, potentials and flows, at fixed k and converged (pairs stopping
+    at different steps), on a weighted power-law graph and on a grid; the direct form needs
+    one SpMM step per Lanczos step instead of two."""
+    cl, s_cl, t_cl = W.chunglu(20000, 2.1, 20.0, 200000, 24, 5, weights="lognormal")
+    gd = F.grid_deleted(40, 0.05, 3)
+    s_g, t_g = F.random_pairs(gd.n, 12, 4)
+    for g, s, t in ((cl, s_cl, t_cl), (gd, s_g, t_g)):
+        G = rd.Graph.from_csr(g)
+        for kw in (dict(k_max=11, fixed_k=True),
+                   dict(k_max=3000, rel_tol=0.0, resid_tol=1e-10 if mode == "fp64" else 1e-6)):
+            ga, ra = G.edge_grad(s, t, None, mode=mode, **kw)
+            steps_direct = G.last_stats()["spmm_launches"]
+            gb, rb = G.edge_grad(s, t, None, mode=mode, potential_mode="replay", **kw)
+            assert np.array_equal(ra, rb)                   # the same forward pass
+            assert G.last_stats()["spmm_launches"] > steps_direct
+            assert np.abs(ga - gb).max() <= tol * np.abs(gb).max(), (g.name, kw, np.abs(ga - gb).max())
+            pa, _ = G.potential(s[:6], t[:6], mode=mode, **kw)
+            pb, _ = G.potential(s[:6], t[:6], mode=mode, potential_mode="replay", **kw)
+            assert np.abs(pa - pb).max() <= tol * np.abs(pb).max()
+            fa, _ = G.flow(s[:6], t[:6], mode=mode, **kw)
+            fb, _ = G.flow(s[:6], t[:6], mode=mode, potential_mode="replay", **kw)
+            assert np.abs(fa - fb).max() <= tol * np.abs(fb).max()
