@@ -214,10 +214,12 @@ def run_reference(args, world, rank):
     return 0
 
 
-def profile_config(rd, name):
+def profile_config(rd, name, call="query"):
     """One SpMM-heavy query of a workload inside cudaProfilerStart/Stop, after a warm-up query
     (which also runs the autotuner), for ncu --profile-from-start off: 4 fixed Lanczos steps
-    over all of the workload's pairs (double-float vectors for the road grid)."""
+    over all of the workload's pairs (double-float vectors for the road grid). With
+    call="grad": instead the configs sweep's gradient call (rd_edge_grad over all of the
+    workload's pairs, rel_tol 1e-6, k_max 200, upstream gradient 1), after a warm-up call."""
     import torch
 
     from graphgen import workloads as W
@@ -228,15 +230,22 @@ def profile_config(rd, name):
     G = rd.Graph.from_csr(g)
     sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
     mode = "df64" if name == "roadgrid4096" else "fp32"
-    kw = dict(mode=mode, k_max=4, fixed_k=True)
-    G.query(sd, td, **kw)
+    if call == "grad":
+        ones = torch.ones(len(s), dtype=torch.float64, device="cuda")
+        mode = "fp32"
+        kw = dict(mode=mode, k_max=200, rel_tol=1e-6)
+        run = lambda: G.edge_grad(sd, td, ones, **kw)  # noqa: E731
+    else:
+        kw = dict(mode=mode, k_max=4, fixed_k=True)
+        run = lambda: G.query(sd, td, **kw)  # noqa: E731
+    run()
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
-    G.query(sd, td, **kw)
+    run()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     st = G.last_stats()
-    print(json.dumps({"profiled": name, "mode": mode, "n": g.n, "nnz": g.nnz, "pairs": len(s),
+    print(json.dumps({"profiled": name, "call": call, "mode": mode, "n": g.n, "nnz": g.nnz, "pairs": len(s),
                       "rhs_tile": st["rhs_tile"], "kernel": st["kernel"], "spmm_bytes_per_launch":
                       st["spmm_bytes"] / max(st["spmm_launches"], 1)}), flush=True)
     G.close()
@@ -336,7 +345,7 @@ def run_config_sweep(rd, timed, only=None):
         G.close()
 
 
-def run_sweeps(which: str, only=None, profile=False):
+def run_sweeps(which: str, only=None, profile=False, profile_call="query"):
     """Extra measurements beyond the main line (one JSON line each):
     scaling  -- Erdos-Renyi and Barabasi-Albert graphs, n = 1e2..1e6, m = n ln n, k = 20 fixed,
                 64 pairs, FP32 (the scalability experiment, Exp-3);
@@ -406,7 +415,7 @@ def run_sweeps(which: str, only=None, profile=False):
             G.close()
     if which in ("configs", "all"):
         if profile:
-            profile_config(rd, only or "chunglu1m")
+            profile_config(rd, only or "chunglu1m", profile_call)
         else:
             run_config_sweep(rd, timed, only)
     if which in ("pm", "all"):
@@ -458,11 +467,13 @@ def main():
     ap.add_argument("--only", default=None,
                     choices=["grid64", "chunglu1m", "rmat24", "roadgrid4096", "chunglu4m_w"],
                     help="with --sweep configs: one workload; with --profile-range: a short profiled query of it")
+    ap.add_argument("--profile-call", default="query", choices=["query", "grad"],
+                    help="with --sweep configs --profile-range: the profiled call (grad: rd_edge_grad)")
     ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "configs", "all"],
                     help="extra measurements instead of the main line")
     args = ap.parse_args()
     if args.sweep:
-        return run_sweeps(args.sweep, args.only, args.profile_range)
+        return run_sweeps(args.sweep, args.only, args.profile_range, args.profile_call)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

@@ -109,6 +109,23 @@ __device__ __forceinline__ void acc_add<df64>(df64& acc, df64 x)
     acc.hi = s.hi;
     acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, x.lo));
 }
+// The same with an FP32 edge weight (a df64 with a zero low part): the product's w.lo x.hi
+// term, an exact zero, is not formed.
+template <typename T>
+__device__ __forceinline__ void acc_mul_add_w(T& acc, float w, T x)
+{
+    acc_mul_add(acc, T(w), x);
+}
+template <>
+__device__ __forceinline__ void acc_mul_add_w<df64>(df64& acc, float w, df64 x)
+{
+    const float p = __fmul_rn(w, x.hi);
+    float e = __fmaf_rn(w, x.hi, -p);  // exact low part of w * x.hi
+    e = __fmaf_rn(w, x.lo, e);
+    const df64 s = df_two_sum(acc.hi, p);
+    acc.hi = s.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
+}
 template <>
 __device__ __forceinline__ void acc_finish<df64>(df64& acc)
 {

@@ -236,13 +236,13 @@ __device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t beg, in
         // general loop below), loading U indices and keeping U gathers in flight per round
         for (int64_t base = beg; base < end; base += (int64_t)NZL * U) {
             int j[U];
-            T wu[U];
+            float wu[U];
             T x[U][VEC];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int64_t e = base + (int64_t)u * NZL + zl;
                 j[u] = e < end ? __ldg(a.col + e) : -1;
-                if constexpr (WEIGHTED) wu[u] = e < end ? (T)__ldg(a.w + e) : T(0);
+                if constexpr (WEIGHTED) wu[u] = e < end ? __ldg(a.w + e) : 0.0f;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -257,7 +257,7 @@ __device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t beg, in
             for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) {
-                    if constexpr (WEIGHTED) acc_mul_add(acc[i], wu[u], x[u][i]);
+                    if constexpr (WEIGHTED) acc_mul_add_w(acc[i], wu[u], x[u][i]);
                     else acc_add(acc[i], x[u][i]);
                 }
             }
@@ -273,12 +273,12 @@ __device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t beg, in
         if constexpr (WEIGHTED) my_w = li < cnt ? __ldg(a.w + base + li) : 0.0f;
         for (int k0 = 0; k0 < cnt; k0 += NZL * U) {
             T x[U][VEC];
-            T wu[U];
+            float wu[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int kk = k0 + zl + u * NZL;
                 const int j = __shfl_sync(mask, my_col, kk & (G - 1), G);
-                if constexpr (WEIGHTED) wu[u] = (T)__shfl_sync(mask, my_w, kk & (G - 1), G);
+                if constexpr (WEIGHTED) wu[u] = __shfl_sync(mask, my_w, kk & (G - 1), G);
                 if (kk < cnt) {
                     ld_gather<T, VEC>(x[u], q + (int64_t)j * ld);
                 } else {
@@ -290,7 +290,7 @@ __device__ __forceinline__ void gather_row(const StepArgs<T>& a, int64_t beg, in
             for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) {
-                    if constexpr (WEIGHTED) acc_mul_add(acc[i], wu[u], x[u][i]);
+                    if constexpr (WEIGHTED) acc_mul_add_w(acc[i], wu[u], x[u][i]);
                     else acc_add(acc[i], x[u][i]);
                 }
             }
@@ -785,14 +785,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
                 }
                 for (int k0 = 0; k0 < cnt; k0 += U) {
                     T x[U][VEC];
-                    T wu[U];
+                    float wu[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         // k0 == 0 when GS < U; otherwise k0 + u < GS
                         const int kk = k0 + u;
                         const int hh = GS >= U ? 0 : u / (GS >= U ? 1 : GS);
                         const uint32_t off = __shfl_sync(mask, my_off[hh], kk % GS, GS);
-                        if constexpr (WEIGHTED) wu[u] = (T)__shfl_sync(mask, my_w[hh], kk % GS, GS);
+                        if constexpr (WEIGHTED) wu[u] = __shfl_sync(mask, my_w[hh], kk % GS, GS);
                         if (kk < cnt) {
 #if RD_GATHER_HINT
                             ld_gather_pol<T, VEC>(x[u], q + (size_t)off * VEC, off < hot_off ? pol_hot : pol_cold);
@@ -830,7 +830,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
                         }
                         if constexpr (WEIGHTED) {
 #pragma unroll
-                            for (int i = 0; i < VEC; ++i) acc_mul_add(acc[i], wu[u], x[u][i]);
+                            for (int i = 0; i < VEC; ++i) acc_mul_add_w(acc[i], wu[u], x[u][i]);
                         } else {
 #pragma unroll
                             for (int i = 0; i < VEC; ++i) acc_add(acc[i], x[u][i]);

@@ -422,7 +422,7 @@ void launch_step_advance(cudaStream_t st, int32_t* step, int limit) { k_step_adv
 template <typename T>
 __device__ __forceinline__ void step0_term(T& acc, const float* w, int64_t e, T q)
 {
-    if (w) acc_mul_add(acc, T(__ldg(w + e)), q);
+    if (w) acc_mul_add_w(acc, __ldg(w + e), q);
     else acc_add(acc, q);
 }
 
