@@ -238,6 +238,43 @@ def test_lanczos_potential_matches_dense():
     np.testing.assert_allclose(phi, ref - ref.mean(), atol=1e-8 * np.abs(ref).max())
 
 
+def test_direct_potential_update_equals_algorithm5_potential():
+    """The recurrence the CUDA path uses for the potential (built during the forward steps:
+    with I - T_i = L D L^T, p_i = v_i + (beta_i/delta_{i-1}) p_{i-1} and
+    x_i = x_{i-1} + ||b|| (g_i/delta_i) p_i) gives, at every k, Algorithm 5's
+    ||b|| V_k (I - T_k)^{-1} e_1, and after D^{-1/2} the oracle's potential; checked here on
+    the oracle's basis and coefficients, with the solve done afresh at each k."""
+    g = F.random_connected(60, 120, 17, "lognormal")
+    s, t, K = 4, 51, 25
+    out = lanczos.lanczos_pair(g, s, t, k_max=K, want_basis=True)
+    V, a, b = out["V"], out["alpha"], out["beta"]
+    k = out["k"]
+    assert k == K
+    deg = np.zeros(g.n)
+    np.add.at(deg, g.rows(), g.w.astype(np.float64))
+    bn = np.sqrt(1 / deg[s] + 1 / deg[t])
+    p = np.zeros(g.n)
+    x = np.zeros(g.n)
+    d_prev = g_prev = None
+    for i in range(k):
+        if i == 0:
+            lam, d, gi = 0.0, 1.0 - a[0], 1.0
+        else:
+            lam = b[i] / d_prev
+            d = (1.0 - a[i]) - b[i] ** 2 / d_prev
+            gi = g_prev * b[i] / d_prev
+        p = V[:, i] + lam * p
+        x = x + bn * (gi / d) * p
+        T = np.diag(a[:i + 1]) + np.diag(b[1:i + 1], 1) + np.diag(b[1:i + 1], -1)
+        e1 = np.zeros(i + 1)
+        e1[0] = 1.0
+        ref = bn * V[:, :i + 1] @ np.linalg.solve(np.eye(i + 1) - T, e1)
+        assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max(), i
+        d_prev, g_prev = d, gi
+    phi = lanczos.lanczos_pair(g, s, t, k_max=K, want_potential=True)["phi"]
+    assert np.abs(x / np.sqrt(deg) - phi).max() <= 1e-12 * np.abs(phi).max()
+
+
 # ---------------------------------------------------- planted mistakes
 
 MUTATIONS = {
