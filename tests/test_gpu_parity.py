@@ -471,10 +471,11 @@ def test_autotuner_first_use_and_arguments(rd):
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
 def test_graph_replay_is_bitwise_the_launch_loop(rd, mode):
-    """Steps replayed from the captured two-step CUDA graph (step index in device memory)
+    """Steps replayed from the captured one-step CUDA graph (step index in device memory)
     give bitwise the results of launching every kernel from the host: compacting query with
-    the error-estimate stop, fixed k (odd, so the last graph half runs idle), the plain
-    path, and the gradient (whose replay pass must regenerate the forward vectors)."""
+    the error-estimate stop, fixed k, the plain path, and the gradient (potential built
+    during the forward steps, or by the replay pass, which must regenerate the forward
+    vectors)."""
     g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 70, 13)
     G = rd.Graph.from_csr(g)
     for kw in (dict(k_max=200, rel_tol=1e-7), dict(k_max=200, rel_tol=0.0, resid_tol=1e-9),
@@ -490,6 +491,10 @@ def test_graph_replay_is_bitwise_the_launch_loop(rd, mode):
     assert np.array_equal(pa.r, pb.r) and np.array_equal(pa.iters, pb.iters)
     ga, ra = G.edge_grad(s[:16], t[:16], None, mode=mode, k_max=200, rel_tol=0.0, resid_tol=1e-9)
     gb, rb = G.edge_grad(s[:16], t[:16], None, mode=mode, k_max=200, rel_tol=0.0, resid_tol=1e-9, graph=False)
+    assert np.array_equal(ra, rb) and np.array_equal(ga, gb)
+    kw = dict(mode=mode, k_max=200, rel_tol=0.0, resid_tol=1e-9, potential_mode="replay")
+    ga, ra = G.edge_grad(s[:16], t[:16], None, **kw)
+    gb, rb = G.edge_grad(s[:16], t[:16], None, graph=False, **kw)
     assert np.array_equal(ra, rb) and np.array_equal(ga, gb)
     ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=200, stop_tol=1e-14, threads=0)
     assert rel(a.r, ref).max() < 1e-7        # the last query's rel_tol
