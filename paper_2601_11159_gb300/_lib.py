@@ -11,6 +11,8 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librd.so")
 
+RD_ABI_VERSION = 1
+
 RD_OK = 0
 RD_WARN_NOT_CONVERGED = 1
 RD_ERR_INVALID_ARG = -1

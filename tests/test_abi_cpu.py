@@ -106,3 +106,45 @@ def test_ctypes_structs_match_header(cname, pyname):
     assert [n for _, n in hdr] == [n for n, _ in py]
     for (t, n), (_, pt) in zip(hdr, py):
         assert ctype[t] == pt, (cname, n, t, pt)
+
+
+def test_header_constants_match_the_binding():
+    """Every #define RD_* value in the header equals the binding's constant of that name, and
+    the binding's keyword options set exactly the documented flags."""
+    from paper_2601_11159_gb300 import _lib
+
+    src = open(os.path.join(ROOT, "include", "rd.h")).read()
+    defines = dict(re.findall(r"#define\s+(RD_[A-Z0-9_]+)\s+(\d+)u?", src))
+    assert defines
+    for name, value in defines.items():
+        assert getattr(_lib, name) == int(value), name
+    import paper_2601_11159_gb300 as rd
+
+    base = rd._opts().flags
+    assert base == 0
+    assert rd._opts(sparse_first=False).flags == _lib.RD_Q_DENSE_FIRST
+    assert rd._opts(potential_mode="replay").flags == _lib.RD_Q_REPLAY_POTENTIAL
+    assert rd._opts(graph=False, tune=False).flags == _lib.RD_Q_NO_GRAPH | _lib.RD_Q_NO_TUNE
+    assert rd._opts(estimate="delayed").flags == _lib.RD_Q_EST_DELAYED
+    with pytest.raises(ValueError):
+        rd._opts(potential_mode="stored")
+    with pytest.raises(ValueError):
+        rd._opts(mode="fp16")
+
+
+def test_bench_uses_the_traffic_summary_only_where_it_was_taken():
+    """bench.py reports the committed ncu DRAM traffic only for the kernel source, workload and
+    SpMM launches per query it was captured on."""
+    import json
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    d = json.load(open(os.path.join(ROOT, "profiles", "spmm_traffic.json")))
+    n = d["spmm_launches_per_query"]
+    same_source = d["kernel_source_sha1"] == bench.kernel_source_hash()
+    got = bench.load_traffic(d["workload"], n)
+    assert got == (d["dram_bytes_per_launch"] if same_source else None)
+    assert bench.load_traffic(d["workload"], n + 1) is None
+    assert bench.load_traffic("chunglu1000000_128pairs", n) is None
