@@ -207,8 +207,9 @@ rd_status rd_query(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npai
  * dr/dw_uv = -(phi(u) - phi(v))^2 and phi = sqrt(1/d_s+1/d_t) D^{-1/2} V_k (I-T_k)^{-1} e_1,
  * the Lanczos potential of Section 6.3 (the one Algorithm 5 starts from). Both stored copies of an
  * edge get the same value, so moving both copies by delta changes the objective by
- * delta * (sum of the two). phi is rebuilt by a second Lanczos pass that replays the
- * stored alpha/beta (no basis V_k is kept).
+ * delta * (sum of the two). phi is built during the forward steps from the LDL^T factors of
+ * I - T_i (no basis V_k is kept and no second pass runs); RD_Q_REPLAY_POTENTIAL instead
+ * rebuilds it by a second Lanczos pass that replays the stored alpha/beta.
  *  grad_r     : double[npairs] host or device, or NULL for all ones.
  *  grad_w_out : float[nnz_created] host or device (nnz as passed to create; entries that
  *               were self-loops get 0).
