@@ -29,7 +29,10 @@ BASE_SEED = 20260101
 
 
 def cache_dir() -> str:
-    d = os.environ.get("RD_GRAPH_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "rd_graphs"))
+    """Where generated workload graphs are kept between runs: $RD_GRAPH_CACHE, else the
+    repository's own .graph_cache/ (not versioned)."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    d = os.environ.get("RD_GRAPH_CACHE", os.path.join(root, ".graph_cache"))
     os.makedirs(d, exist_ok=True)
     return d
 
