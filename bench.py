@@ -347,6 +347,46 @@ def run_config_sweep(rd, timed, only=None):
         G.close()
 
 
+def condition_number(g, tol: float = 1e-6):
+    """kappa = 2/(1 - mu_2), mu_2 the second-largest eigenvalue of Ahat = D^{-1/2} W D^{-1/2}
+    (the largest is 1, eigenvector D^{1/2} 1, deflated here): scipy eigsh on the host, FP64."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+
+    w = np.ones(g.nnz) if g.w is None else g.w.astype(np.float64)
+    A = sp.csr_matrix((w, g.col, g.row_ptr), shape=(g.n, g.n))
+    d = np.asarray(A.sum(axis=1)).ravel()
+    isd = 1.0 / np.sqrt(d)
+    Ah = sp.diags(isd) @ A @ sp.diags(isd)
+    u = np.sqrt(d) / np.linalg.norm(np.sqrt(d))
+    op = sla.LinearOperator(Ah.shape, matvec=lambda x: Ah @ x - u * (u @ x), dtype=np.float64)
+    mu2 = float(sla.eigsh(op, k=1, which="LA", tol=tol, return_eigenvectors=False, maxiter=20000).max())
+    return mu2, 2.0 / (1.0 - mu2)
+
+
+def run_kappa(only=None):
+    """Condition numbers of the synthetic workloads (host only). The road grid's gap (about
+    1e-7) is beyond eigsh in reasonable time: its line gives the undeleted 4096^2 grid's value
+    8 N^2 / pi^2 (mu_2 = 1 - pi^2/(4 N^2) to leading order) as an estimate."""
+    import math
+
+    from graphgen import workloads as W
+
+    for name, make in (("grid64", W.grid64), ("chunglu1m", W.chunglu1m), ("chunglu4m_w", W.chunglu4m_w),
+                       ("rmat24", W.rmat24)):
+        if only and name != only:
+            continue
+        g = make()[0]
+        t0 = time.time()
+        mu2, kappa = condition_number(g)
+        print(json.dumps({"sweep": "kappa", "workload": name, "n": g.n, "nnz": g.nnz, "mu2": mu2, "kappa": kappa,
+                          "method": "eigsh (deflated Ahat)", "host_s": round(time.time() - t0, 1)}), flush=True)
+    if not only or only == "roadgrid4096":
+        N = 4096
+        print(json.dumps({"sweep": "kappa", "workload": "roadgrid4096", "kappa": 8 * N * N / math.pi ** 2,
+                          "method": "estimate: undeleted 4096^2 grid, 8 N^2 / pi^2"}), flush=True)
+
+
 def run_sweeps(which: str, only=None, profile=False, profile_call="query"):
     """Extra measurements beyond the main line (one JSON line each):
     scaling  -- Erdos-Renyi and Barabasi-Albert graphs, n = 1e2..1e6, m = n ln n, k = 20 fixed,
@@ -471,9 +511,11 @@ def main():
                     help="with --sweep configs: one workload; with --profile-range: a short profiled query of it")
     ap.add_argument("--profile-call", default="query", choices=["query", "grad"],
                     help="with --sweep configs --profile-range: the profiled call (grad: rd_edge_grad)")
-    ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "configs", "all"],
-                    help="extra measurements instead of the main line")
+    ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "configs", "kappa", "all"],
+                    help="extra measurements instead of the main line (kappa: host only)")
     args = ap.parse_args()
+    if args.sweep == "kappa":
+        return run_kappa(args.only)
     if args.sweep:
         return run_sweeps(args.sweep, args.only, args.profile_range, args.profile_call)
     if args.warmup < 3:
