@@ -187,6 +187,27 @@ def cpu_oracle(g, s, t, sample: int, threads: int = 0):
     return r, k, used, dt
 
 
+def host_info() -> dict:
+    """The host the oracle timings ran on: architecture, CPU model (x86 "model name", or the
+    Arm implementer/part codes), logical CPUs."""
+    import platform
+
+    model = None
+    try:
+        fields = {}
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields.setdefault(k.strip(), v.strip())
+        model = fields.get("model name") or (
+            f"implementer {fields.get('CPU implementer')} part {fields.get('CPU part')}"
+            if "CPU part" in fields else None)
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "model": model or platform.processor() or None,
+            "nproc": os.cpu_count()}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -207,7 +228,7 @@ def run_reference(args, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "chunglu1m_256pairs", "n": g.n, "nnz": g.nnz, "pairs_per_step": sample,
                    "sample": f"{sample} of the 256 pairs per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "host": host_info(),
                          "sample": f"{sample} pairs of the 256-pair workload per step, stop at relative "
                                    f"increment 1e-9"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -651,7 +672,7 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
         r_or, k_or, used, dt = cpu_oracle(g, s_np, t_np, cs)
         rel = np.abs(r_gpu[:cs] - r_or) / np.abs(r_or)
         max_rel = float(rel.max())
-        cpu = {"value": cs / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
+        cpu = {"value": cs / dt, "unit": UNIT, "cores": int(used), "kind": "oracle", "host": host_info(),
                "sample": f"{cs} of the {P} pairs, FP64 C Lanczos, stop at relative increment 1e-9; the same "
                          f"run gives the reference values for max_rel_err",
                "max_rel_err_gpu_vs_oracle": max_rel, "median_rel_err_gpu_vs_oracle": float(np.median(rel))}
