@@ -4,7 +4,6 @@ job's time is the max over ranks."""
 import os
 import socket
 
-import numpy as np
 import pytest
 
 

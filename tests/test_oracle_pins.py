@@ -7,7 +7,6 @@ the structural identities of Proposition lanczos_guarantee and Lemma
 lz_quadratic_err, and brute-force finite differences for the gradient.
 """
 import os
-import re
 import subprocess
 
 import numpy as np
