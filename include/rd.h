@@ -62,7 +62,14 @@ typedef enum {
 typedef enum {
     RD_MODE_FP64 = 0,        /* vectors, SpMV/SpMM and all scalars in FP64 */
     RD_MODE_FP32V_FP64S = 1, /* vectors and SpMM in FP32; alpha, beta, T_k, its solve and every
-                                cross-thread reduction in FP64 */
+                                cross-thread reduction in FP64. Accuracy floor: the FP32 rounding of
+                                the vectors limits the attainable relative error of r, and the
+                                floor grows with the condition number kappa = 2/(1 - mu_2(Ahat)):
+                                below 1e-7 at kappa ~ 10 (power-law graphs), about 5e-6 on a 64x64
+                                grid (kappa ~ 3e3), about 2e-4 on a 4096x4096 road-like grid
+                                (kappa ~ 1.4e7). Tolerances below the floor are not met there (the
+                                iteration runs on, or stops on an estimate that is not a bound): use
+                                RD_MODE_FP64 or RD_MODE_DF64 for large-kappa graphs */
     RD_MODE_DF64 = 2         /* rd_query only (the other calls run it as RD_MODE_FP64): vectors
                                 stored as pairs of FP32 numbers (hi + lo, about 48 significant
                                 bits) with the element arithmetic on the FP32 units by error-free
@@ -115,7 +122,9 @@ typedef struct {
                               S_k = e_1^T (I-T_k)^{-1} e_1 and rho the largest of the last three
                               ratios d_j / d_{j-1} (at least 1/2), d_k * rho / (1 - rho)^2 / S_k,
                               the tail of a geometric series with a margin for slow decay; not
-                              a bound (RD_Q_EST_DELAYED selects the delayed-sum estimate) */
+                              a bound (RD_Q_EST_DELAYED selects the delayed-sum estimate); with
+                              RD_MODE_FP32V_FP64S on large-kappa graphs the FP32 floor (see rd_mode)
+                              can exceed rel_tol, and the pair then stops with an error above it */
     double resid_tol;      /* stop when ||b - (I - Ahat) x_k|| / ||b|| <= resid_tol (0 = off) */
     int32_t mode;          /* rd_mode */
     int32_t rhs_tile;      /* right-hand-side columns per SpMM sweep; 0 = tuned */
@@ -129,7 +138,10 @@ typedef struct {
                               3 = row-group visiting the rows by decreasing degree (the row groups
                               of a warp then hold rows of equal length), 4 = warp-per-task SpMV
                               (one column only: RD_Q_PLAIN or one pair; RD_ERR_UNSUPPORTED
-                              otherwise); with one column the fixed rule (RD_Q_NO_TUNE) takes 4 */
+                              otherwise), 5 = row-stream with asynchronous copies of the gathered
+                              rows into a shared-memory ring (FP32 vectors and 16 to 128 columns per
+                              slab only; RD_ERR_UNSUPPORTED otherwise; with one column it takes 4);
+                              with one column the fixed rule (RD_Q_NO_TUNE) takes 4 */
 } rd_query_opts;
 
 /* Per-call statistics of the last rd_query / rd_edge_grad / rd_potential on g. */
@@ -141,7 +153,7 @@ typedef struct {
     int32_t rhs_tile;        /* configuration used */
     int32_t rows_per_warp;
     int32_t nnz_lanes;       /* lanes that share one row's nonzeros */
-    int32_t kernel;          /* SpMM kernel used, numbered as rd_query_opts::kernel (1 .. 4) */
+    int32_t kernel;          /* SpMM kernel used, numbered as rd_query_opts::kernel (1 .. 5) */
     int64_t ld;              /* padded number of right-hand-side columns (vector row stride) */
     double spmm_bytes;       /* algorithmic bytes of all SpMM launches of the call, each
                                 4*nnz (+4*nnz weights) + 8*(n+1) + 3*ld*n*sizeof(element) with the
@@ -265,8 +277,10 @@ rd_status rd_flow(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npair
  *  n, nnz, row_ptr, col_idx, weights : symmetric CSR as for rd_graph_create, DEVICE pointers;
  *                    self-loops are rejected (RD_ERR_UNSUPPORTED) since the CSR is used as is.
  *  s, t            : int32[npairs] device pointers.
- *  opts            : as rd_query (RD_Q_PROFILE is ignored; the SpMM kernel is row-group;
- *                    disconnected pairs are not labelled and end as RD_ERR_NUMERIC).
+ *  opts            : as rd_query, except: RD_Q_PROFILE is ignored; the SpMM kernel is
+ *                    row-group; RD_MODE_DF64 runs as RD_MODE_FP64 (FP64 vectors, the same
+ *                    accuracy class, 8-byte elements in the same scratch); disconnected pairs
+ *                    are not labelled and end as RD_ERR_NUMERIC.
  *  r_out           : double[npairs] device pointer; iters_out: int32[npairs] device or NULL.
  * Limits: the scratch must hold 24*n bytes of degrees plus the query workspace
  * (2*n*ld vector elements, (k_max+1)*4*ld coefficients, the per-pair state); a request that
@@ -274,7 +288,12 @@ rd_status rd_flow(rd_graph* g, const int32_t* s, const int32_t* t, int64_t npair
  * nothing. Host pointers are rejected with RD_ERR_INVALID_ARG.
  * Set-up: the first call on each device looks up the array's device address with
  * cudaGetSymbolAddress (with that device current); make that first call before any
- * stream capture. Sharing: every call uses the same array, which keeps the previous
+ * stream capture. The address is kept for the life of the process: it does not survive
+ * cudaDeviceReset (or any other destruction of the device's primary context), after which
+ * this entry point must not be called again in that process.
+ * Polls: the call waits on the stream for per-pair convergence counts every chunk_steps
+ * steps and copies them into pageable host memory (it allocates no pinned buffer), so each
+ * poll is a synchronous copy; the outputs are ready on return. Sharing: every call uses the same array, which keeps the previous
  * call's contents (the call clears what must start at zero itself); calls that overlap on
  * the GPU (other streams, other host threads) race on it. Returns as rd_query. */
 rd_status rd_query_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,

@@ -121,7 +121,7 @@ def _opts(k_max=1000, rel_tol=1e-7, resid_tol=0.0, mode="fp32", rhs_tile=0, rows
     o.rhs_tile = int(rhs_tile)
     o.rows_per_warp = int(rows_per_warp)
     o.chunk_steps = int(chunk_steps)
-    o.kernel = ({"tuned": 0, "group": 1, "stream": 2, "group_sorted": 3, "tasks": 4}.get(kernel, kernel)
+    o.kernel = ({"tuned": 0, "group": 1, "stream": 2, "group_sorted": 3, "tasks": 4, "async": 5}.get(kernel, kernel)
                 if isinstance(kernel, str) else int(kernel))
     o.flags = ((RD_Q_FIXED_K if fixed_k else 0) | (0 if deflate else RD_Q_NO_DEFLATE) |
                (RD_Q_PLAIN if plain else 0) | (RD_Q_PROFILE if profile else 0) |
@@ -258,29 +258,51 @@ def power_method(handle: int, s, t, steps: int, mode: str = "fp64", history: boo
     return r, (None if hist is None else hist.reshape(steps + 1, P))
 
 
+def _noalloc_tensor(x, name: str, dtype, min_numel: int = 0):
+    """Pointer of a tensor handed to rd_query_noalloc as is: a contiguous CUDA tensor of the
+    exact dtype on the current device. Nothing is converted, because a conversion would
+    allocate device memory, which is what this entry point's callers cannot do."""
+    torch = _torch()
+    if not (_is_torch(x) and x.is_cuda):
+        raise TypeError(f"query_noalloc: {name} must be a CUDA tensor")
+    if x.device.index != torch.cuda.current_device():
+        raise ValueError(f"query_noalloc: {name} is on {x.device}, not on the current device")
+    if x.dtype != dtype:
+        raise TypeError(f"query_noalloc: {name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise TypeError(f"query_noalloc: {name} must be contiguous")
+    if x.numel() < min_numel:
+        raise ValueError(f"query_noalloc: {name} holds {x.numel()} elements, needs at least {min_numel}")
+    return x.data_ptr() if x.numel() > 0 else None
+
+
 def query_noalloc(row_ptr, col, w, s, t, stream=None, **kw):
     """rd_query_noalloc for callers that cannot allocate device memory: every array must be a
-    CUDA tensor (the graph is used in place, no handle is created). Returns (r, iters) as CUDA
-    tensors; the caller may pass ``out=(r, iters)`` to reuse preallocated outputs."""
+    contiguous CUDA tensor of the C ABI's type on the current device (row_ptr int64, col int32,
+    w float32 or None, s and t int32 of equal length); nothing is converted. The graph is used
+    in place and no handle is created. Returns (r, iters) as CUDA tensors; pass
+    ``out=(r, iters)`` (float64 and int32, at least len(s) elements each) to reuse
+    preallocated outputs, so that the call itself allocates nothing."""
+    torch = _torch()
     out = kw.pop("out", None)
-    for x in (row_ptr, col, s, t) + (() if w is None else (w,)):
-        if not (_is_torch(x) and x.is_cuda):
-            raise TypeError("query_noalloc takes CUDA tensors only")
-    rp, k1 = _arr(row_ptr, np.int64)
-    cp, k2 = _arr(col, np.int32)
-    wp, k3 = _arr(w, np.float32)
-    sp, ks = _arr(s, np.int32)
-    tp_, kt = _arr(t, np.int32)
-    n = k1.numel() - 1
-    P = ks.numel()
+    rp = _noalloc_tensor(row_ptr, "row_ptr", torch.int64, 1)
+    cp = _noalloc_tensor(col, "col", torch.int32)
+    wp = None if w is None else _noalloc_tensor(w, "w", torch.float32, col.numel())
+    sp = _noalloc_tensor(s, "s", torch.int32)
+    P = s.numel()
+    tp_ = _noalloc_tensor(t, "t", torch.int32)
+    if t.numel() != P:
+        raise ValueError(f"query_noalloc: s and t differ in length ({P} and {t.numel()})")
     if out is None:
         r, rp_ = _out(True, P, np.float64)
         it, ip = _out(True, P, np.int32)
     else:
         r, it = out
-        rp_, ip = (r.data_ptr() if P else None), (it.data_ptr() if P else None)
+        rp_ = _noalloc_tensor(r, "out[0] (r)", torch.float64, P)
+        ip = _noalloc_tensor(it, "out[1] (iters)", torch.int32, P)
+    n = row_ptr.numel() - 1
     o = _opts(**kw)
-    st = lib().rd_query_noalloc(n, k2.numel(), rp, cp, wp, sp, tp_, P, C.byref(o), rp_, ip, _stream_ptr(stream))
+    st = lib().rd_query_noalloc(n, col.numel(), rp, cp, wp, sp, tp_, P, C.byref(o), rp_, ip, _stream_ptr(stream))
     _check(st, "rd_query_noalloc")
     return r, it
 
@@ -357,8 +379,9 @@ def _make_autograd():
     class ResistanceDistance(torch.autograd.Function):
         """r = ResistanceDistance.apply(w, graph, s, t, opts): resistance distances of the pairs under
         edge weights ``w`` (float32 CUDA tensor, one per stored CSR entry, kept symmetric). The
-        backward pass calls rd_edge_grad, which recomputes the forward recurrence and rebuilds the
-        potentials by a replay pass."""
+        backward pass calls rd_edge_grad, which recomputes the forward recurrence and builds the
+        potentials during those steps from the LDL^T factors of I - T_i (the direct update; no
+        basis is stored and no second pass runs unless opts asks for potential_mode="replay")."""
 
         @staticmethod
         def forward(ctx, w, graph, s, t, opts=None):

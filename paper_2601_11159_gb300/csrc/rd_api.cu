@@ -343,6 +343,7 @@ struct Plan {
 // rd_query_opts::kernel / rd_call_stats::kernel number of a configuration.
 static int kernel_code(const SpmmCfg& c)
 {
+    if (c.kind == 3) return 5;
     if (c.kind == 2) return 4;
     if (c.kind == 1) return 2;
     return c.order ? 3 : 1;
@@ -386,7 +387,8 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     if (plain || P == 1) {
         c.vec = 1;
         c.gs = 1;
-        if ((o.kernel == 0 || o.kernel == 4) && g->ntasks > 0) {  // warp-per-task SpMV
+        // warp-per-task SpMV (also for kernel 5, whose slabs need more than one column)
+        if ((o.kernel == 0 || o.kernel == 4 || o.kernel == 5) && g->ntasks > 0) {
             c.nzl = 1;
             c.kind = 2;
             return c;
@@ -404,6 +406,14 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
     if (o.kernel == 4) {  // single-column only: no such tile (make_plan reports it)
         c.kind = 2;
         c.vec = 2;
+        return c;
+    }
+    if (o.kernel == 5) {  // async row-stream: FP32 vectors, tiles of 16 to 128 columns
+        int tpa = o.rhs_tile > 0 ? o.rhs_tile : (P <= 16 ? 16 : (P <= 32 ? 32 : (P <= 64 ? 64 : 128)));
+        c.vec = fp64 ? 2 : 4;  // an FP64 request names no instantiated tile (make_plan reports it)
+        c.gs = std::max(1, tpa / c.vec);
+        c.nzl = 1;
+        c.kind = 3;
         return c;
     }
     int tp = o.rhs_tile;
@@ -439,7 +449,7 @@ static rd_status make_plan_cfg(rd_graph* g, int64_t P, const rd_query_opts& o, c
     int bps = spmm_blocks_per_sm(pl->cfg, g->weighted, false, pl->prec);
     if (bps < 1) bps = 1;
     int64_t gm = (int64_t)bps * g->sm_count;
-    int64_t units = pl->cfg.kind == 1 ? g->ntasks : g->n;  // rows or tasks, one per row group
+    int64_t units = pl->cfg.kind == 1 || pl->cfg.kind == 3 ? g->ntasks : g->n;  // rows or tasks, one per row group
     int64_t per_block = rows_per_block;
     if (pl->cfg.kind == 2) {  // one task per warp
         units = g->ntasks;
@@ -1174,8 +1184,8 @@ static rd_status validate_common(rd_graph* g, const int32_t* s, const int32_t* t
         set_error("k_max must be in [1, 2^22]");
         return RD_ERR_INVALID_ARG;
     }
-    if (o->kernel < 0 || o->kernel > 4) {
-        set_error("kernel must be 0, 1, 2, 3 or 4");
+    if (o->kernel < 0 || o->kernel > 5) {
+        set_error("kernel must be 0, 1, 2, 3, 4 or 5");
         return RD_ERR_INVALID_ARG;
     }
     if (o->mode != RD_MODE_FP64 && o->mode != RD_MODE_FP32V_FP64S && o->mode != RD_MODE_DF64) {
@@ -1229,6 +1239,11 @@ static std::vector<SpmmCfg> tune_candidates(const rd_graph* g, int64_t width, bo
             if (gs * z <= 32)
                 for (int o : {0, 1}) add(vec, gs, z, 0, o);
     }
+    // async row-stream (FP32 vectors): column slabs of 16 to 128 columns, down to an eighth
+    // of the width (narrow slabs keep the gathered slab in L2)
+    if (!fp64)
+        for (int64_t tp = std::max<int64_t>(16, width / 8); tp <= std::min<int64_t>(width, 128); tp <<= 1)
+            add(4, (int)(tp / 4), 1, 3, 0);
     return v;
 }
 

@@ -35,7 +35,9 @@ rd_status cuda_status(cudaError_t e, const char* what);
 // columns); NZL lanes share the nonzeros of one row; RPW = 32/(GS*NZL) rows
 // are in flight per warp.
 // kind 0: row-group kernel (k_spmm, grid-stride over rows); kind 1: row-stream kernel
-// (k_spmm_rows, grid-stride over tasks of consecutive rows; nzl must be 1).
+// (k_spmm_rows, grid-stride over tasks of consecutive rows; nzl must be 1); kind 2:
+// warp-per-task SpMV (one column); kind 3: row-stream kernel with cp.async gathers into a
+// shared-memory ring (k_spmm_async, FP32 vectors, vec 4, nzl 1).
 struct SpmmCfg {
     int vec = 4, gs = 32, nzl = 1, kind = 0;
     int order = 0;  // row-group kernel: 1 = visit rows by decreasing degree (rd_graph::row_order)
@@ -50,13 +52,14 @@ struct SpmmCfg {
 // Configuration of the heavy-row pre-pass that goes with a step configuration: the same
 // column tile, one whole warp per chunk of a heavy row (GS column lanes x 32/GS nonzero
 // lanes), so that a chunk's gathers are spread over the warp instead of one row group.
+// The async kernel (kind 3) has its own pre-pass with one row group per chunk.
 inline SpmmCfg heavy_cfg(const SpmmCfg& c)
 {
     SpmmCfg h;
     h.vec = c.vec;
     h.gs = c.gs;
-    h.nzl = 32 / c.gs;
-    h.kind = 0;
+    h.nzl = c.kind == 3 ? 1 : 32 / c.gs;
+    h.kind = c.kind == 3 ? 3 : 0;
     return h;
 }
 

@@ -868,6 +868,291 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
     }
 }
 
+// ----------------------------------------------------- async-copy row stream
+// Row-stream SpMM whose gathers are per-lane 16-byte cp.async copies (the non-bulk form:
+// each lane copies its own column segment of a gathered row) into a ring of D slots in
+// shared memory. A lane keeps D gathers in flight without holding them in registers, so
+// three blocks per SM (24 warps, about 190 KB of gathered rows in flight per SM) stay
+// resident; the ring is refilled as each slot is consumed, so the gathers stay in flight
+// across row and round boundaries. Row groups of GS lanes x VEC = 4 FP32 columns walk the
+// same tasks as k_spmm_rows (runs of consecutive light rows, each heavy row alone with its
+// chunk partials from the pre-pass k_spmm_async_heavy), one column slab of TP = 4 GS
+// columns at a time. The three reductions use Kahan accumulators in registers.
+//
+// Ring protocol (per lane; cp.async groups are per thread): every consumption of a slot is
+// followed by exactly one commit (of the refill copy, or of an empty group when there is
+// nothing to refill), and the prologue of a nonzero range commits D groups, so before
+// consuming a slot at most D groups are pending and wait_group(D - 1) completes the oldest,
+// the one that filled this slot. A range ends with no copy in flight (refills are issued
+// only for nonzeros inside the range), so ranges need no drain.
+#ifndef RD_ASYNC_DEPTH
+#define RD_ASYNC_DEPTH 24
+#endif
+#ifndef RD_ASYNC_MINB
+#define RD_ASYNC_MINB 2
+#endif
+constexpr int kAsyncDepth = RD_ASYNC_DEPTH;  // gathers in flight per lane
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float4 lds_f4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a)
+                 : "memory");
+    return v;
+}
+
+template <int GS>
+constexpr size_t async_smem_bytes()
+{
+    return (size_t)kWarps * kAsyncDepth * 32 * 16 + (size_t)kWarps * (4 * GS) * 8;
+}
+
+// Column indices (as row offsets in float4 units) and weights of the D nonzeros of one
+// round starting at `base`: lane gl holds positions gl + h GS (h < NH) of the round.
+template <int GS, bool WEIGHTED>
+struct AsyncRound {
+    static constexpr int NH = (kAsyncDepth + GS - 1) / GS;
+    uint32_t off[NH];
+    float w[NH];
+    __device__ __forceinline__ void load(const StepArgs<float>& a, int base, int end, int gl, uint32_t ldv)
+    {
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const int pos = h * GS + gl;
+            const bool ok = pos < kAsyncDepth && base + pos < end;
+            off[h] = ok ? (uint32_t)__ldg(a.col + base + pos) * ldv : 0u;
+            if constexpr (WEIGHTED) w[h] = ok ? __ldg(a.w + base + pos) : 0.0f;
+        }
+    }
+    // value held for round position u by its owner lane (u / GS selects the register)
+    __device__ __forceinline__ uint32_t off_at(int u) const
+    {
+        uint32_t v = off[0];
+#pragma unroll
+        for (int h = 1; h < NH; ++h)
+            if (u >= h * GS) v = off[h];
+        return v;
+    }
+    __device__ __forceinline__ float w_at(int u) const
+    {
+        float v = w[0];
+#pragma unroll
+        for (int h = 1; h < NH; ++h)
+            if (u >= h * GS) v = w[h];
+        return v;
+    }
+};
+
+// Stream the nonzeros [eb, ee) of one row group through the ring: `enter(e)` runs before
+// nonzero e is added (row epilogues at row boundaries), then acc += w_e * q[col_e, slab].
+template <int GS, bool WEIGHTED, class Enter>
+__device__ __forceinline__ void async_stream(const StepArgs<float>& a, const float* q, uint32_t ldv, int eb, int ee,
+                                             uint32_t ring, int gl, unsigned mask, float (&acc)[4], Enter&& enter)
+{
+    constexpr int D = kAsyncDepth;
+    constexpr uint32_t SS = 32 * 16;  // slot stride: one float4 per lane of the warp
+    using R = AsyncRound<GS, WEIGHTED>;
+    R cur, nxt, nn;
+    cur.load(a, eb, ee, gl, ldv);
+    nxt.load(a, eb + D, ee, gl, ldv);
+    for (int u = 0; u < D; ++u) {
+        const uint32_t o = __shfl_sync(mask, cur.off_at(u), u % GS, GS);
+        if (eb + u < ee) cp_async16(ring + u * SS, q + (size_t)o * 4);
+        cp_async_commit();
+    }
+    for (int base = eb; base < ee; base += D) {
+        nn.load(a, base + 2 * D, ee, gl, ldv);
+        const int cnt = ee - base < D ? ee - base : D;
+        for (int u = 0; u < cnt; ++u) {
+            const int e = base + u;
+            float wv = 1.0f;
+            if constexpr (WEIGHTED) wv = __shfl_sync(mask, cur.w_at(u), u % GS, GS);
+            const uint32_t o = __shfl_sync(mask, nxt.off_at(u), u % GS, GS);
+            cp_async_wait<D - 1>();
+            const float4 x = lds_f4(ring + u * SS);
+            enter(e);
+            if constexpr (WEIGHTED) {
+                acc[0] = fmaf(wv, x.x, acc[0]);
+                acc[1] = fmaf(wv, x.y, acc[1]);
+                acc[2] = fmaf(wv, x.z, acc[2]);
+                acc[3] = fmaf(wv, x.w, acc[3]);
+            } else {
+                acc[0] += x.x;
+                acc[1] += x.y;
+                acc[2] += x.z;
+                acc[3] += x.w;
+            }
+            if (e + D < ee) cp_async16(ring + u * SS, q + (size_t)o * 4);
+            cp_async_commit();
+        }
+        cur = nxt;
+        nxt = nn;
+    }
+}
+
+// Heavy-row pre-pass of the async kernel: the chunk partials heavy_part[chunk, slab].
+template <int GS, bool WEIGHTED>
+__global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async_heavy(const StepArgs<float> a)
+{
+    constexpr int TP = 4 * GS;
+    constexpr int NG = 32 / GS;
+    extern __shared__ __align__(16) float smem_f[];
+    if (step_inactive(a)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % GS, grp = lane / GS;
+    const unsigned mask = group_mask<GS, 1>(lane);
+    const uint32_t ring = smem_addr(smem_f) + (uint32_t)(warp * kAsyncDepth * 32 + lane) * 16u;
+    const int64_t ngroups = (int64_t)gridDim.x * kWarps * NG;
+    const int64_t gid = ((int64_t)blockIdx.x * kWarps + warp) * NG + grp;
+    const int nslab = (int)(a.ld / TP);
+    const uint32_t ldv = (uint32_t)(a.ld / 4);
+    for (int slab = 0; slab < nslab; ++slab) {
+        const int64_t c0 = (int64_t)slab * TP + gl * 4;
+        const float* q = a.qcur + c0;
+        for (int64_t ch = gid; ch < a.n_chunks; ch += ngroups) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            async_stream<GS, WEIGHTED>(a, q, ldv, a.chunk_beg[ch], a.chunk_end[ch], ring, gl, mask, acc,
+                                       [](int) {});
+            st_plain<float, 4>(a.heavy_part + ch * a.ld + c0, acc);
+        }
+    }
+}
+
+// Main kernel: W = D^{-1} W_adj q_i - beta_i q_{i-1} over q_{i-1}, and the block partials of
+// sum d W q_i, sum d W^2, sum d W per column (slab by slab).
+template <int GS, bool WEIGHTED>
+__global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const StepArgs<float> a)
+{
+    constexpr int TP = 4 * GS;
+    constexpr int NG = 32 / GS;
+    extern __shared__ __align__(16) float smem_f[];
+    double(&red)[kWarps][TP] = *reinterpret_cast<double(*)[kWarps][TP]>(smem_f + kWarps * kAsyncDepth * 32 * 4);
+    if (step_inactive(a)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % GS, grp = lane / GS;
+    const unsigned mask = group_mask<GS, 1>(lane);
+    const uint32_t ring = smem_addr(smem_f) + (uint32_t)(warp * kAsyncDepth * 32 + lane) * 16u;
+    const int ngroups = gridDim.x * kWarps * NG;
+    const int gid = (blockIdx.x * kWarps + warp) * NG + grp;
+    const int nslab = (int)(a.ld / TP);
+    const int64_t ld = a.ld;
+    const uint32_t ldv = (uint32_t)(ld / 4);
+    const int ntasks = (int)a.ntasks;
+
+    for (int slab = 0; slab < nslab; ++slab) {
+        const int64_t c0 = (int64_t)slab * TP + gl * 4;
+        float bt[4];
+        ld_plain<float, 4>(bt, step_cf_beta(a) + c0);
+        Acc<float> sA[4], sB[4], sC[4];
+        const float* q = a.qcur + c0;
+        for (int task = gid; task < ntasks; task += ngroups) {
+            const int r0 = a.task_row[task], r1 = a.task_row[task + 1];
+            const int eb = (int)a.row_ptr[r0], ee = (int)a.row_ptr[r1];
+            float acc[4] = {0.f, 0.f, 0.f, 0.f}, qp[4], qc[4];
+            if (r1 == r0 + 1 && ee - eb > a.heavy_thr) {
+                ld_stream<float, 4>(qp, a.qprev_w + (int64_t)r0 * ld + c0);
+                ld_gather<float, 4>(qc, q + (int64_t)r0 * ld);
+                heavy_row_sum<float, 4, 1>(a, r0, c0, 0, acc);
+                row_epilogue<float, 4>(a, r0, c0, a.invdeg[r0], a.deg[r0], acc, bt, qp, qc, sA, sB, sC);
+                continue;
+            }
+            // row window: lane gl holds row_ptr[w0 + gl + 1], 1/d and d of row w0 + gl
+            int w0 = r0;
+            int my_end = (w0 + gl < r1) ? (int)a.row_ptr[w0 + gl + 1] : ee;
+            float my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : 0.f;
+            float my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : 0.f;
+            int row = r0;
+            int row_end = __shfl_sync(mask, my_end, 0, GS);
+            ld_stream<float, 4>(qp, a.qprev_w + (int64_t)row * ld + c0);
+            ld_gather<float, 4>(qc, q + (int64_t)row * ld);
+            // close the current row and open the next one
+            auto next_row = [&]() {
+                const int wi = row - w0;
+                const float invd = __shfl_sync(mask, my_invd, wi, GS);
+                const float du = __shfl_sync(mask, my_deg, wi, GS);
+                row_epilogue<float, 4>(a, row, c0, invd, du, acc, bt, qp, qc, sA, sB, sC);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] = 0.f;
+                ++row;
+                if (row >= r1) return;
+                if (row - w0 >= GS) {  // refill the row window
+                    w0 = row;
+                    my_end = (w0 + gl < r1) ? (int)a.row_ptr[w0 + gl + 1] : ee;
+                    my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : 0.f;
+                    my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : 0.f;
+                }
+                row_end = __shfl_sync(mask, my_end, row - w0, GS);
+                ld_stream<float, 4>(qp, a.qprev_w + (int64_t)row * ld + c0);
+                ld_gather<float, 4>(qc, q + (int64_t)row * ld);
+            };
+            async_stream<GS, WEIGHTED>(a, q, ldv, eb, ee, ring, gl, mask, acc, [&](int e) {
+                while (e >= row_end) next_row();
+            });
+            while (row < r1) next_row();  // the last row (and rows without nonzeros after it)
+        }
+        if (a.do_reduce) block_partials<float, 4, GS, TP>(a, sA, sB, sC, red, slab, lane, warp, gl);
+    }
+}
+
+template <int GS>
+void async_smem_attr()
+{
+    constexpr size_t sm = async_smem_bytes<GS>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_spmm_async<GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_spmm_async<GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_spmm_async_heavy<GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_spmm_async_heavy<GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+}
+
+template <int GS>
+bool launch_async_cfg(bool weighted, bool heavy, int grid, cudaStream_t st, const StepArgs<float>& a)
+{
+    constexpr size_t sm = async_smem_bytes<GS>();
+    async_smem_attr<GS>();
+    if (heavy) {
+        if (weighted) k_spmm_async_heavy<GS, true><<<grid, kBlock, sm, st>>>(a);
+        else k_spmm_async_heavy<GS, false><<<grid, kBlock, sm, st>>>(a);
+    } else {
+        if (weighted) k_spmm_async<GS, true><<<grid, kBlock, sm, st>>>(a);
+        else k_spmm_async<GS, false><<<grid, kBlock, sm, st>>>(a);
+    }
+    return true;
+}
+
+template <int GS>
+int occupancy_async_cfg(bool weighted, bool heavy)
+{
+    int nb = 0;
+    constexpr size_t sm = async_smem_bytes<GS>();
+    async_smem_attr<GS>();
+    if (heavy) {
+        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async_heavy<GS, true>, kBlock, sm);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async_heavy<GS, false>, kBlock, sm);
+    } else {
+        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async<GS, true>, kBlock, sm);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async<GS, false>, kBlock, sm);
+    }
+    return nb;
+}
+
 // Single-column SpMV (one pair per launch, ld = 1). One warp per task (consecutive rows
 // with at most kTaskNnz nonzeros, or one heavy row): the lanes stride over the task's
 // nonzeros with coalesced index loads and 8 gathers in flight per lane, leaving the

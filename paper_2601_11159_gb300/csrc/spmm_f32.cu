@@ -27,9 +27,23 @@ namespace rd {
     X(4, 32, 1)           \
     X(8, 32, 1)
 
+#define RD_F32_ASYNC(X) \
+    X(4)                \
+    X(8)                \
+    X(16)               \
+    X(32)
+
 bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
                      const StepArgs<float>& a)
 {
+    if (c.kind == 3) {
+        if (c.vec != 4 || c.nzl != 1) return false;
+#define X(G) \
+    if (c.gs == G) return launch_async_cfg<G>(weighted, heavy, grid, st, a);
+        RD_F32_ASYNC(X)
+#undef X
+        return false;
+    }
     if (c.kind == 2 && !heavy) return launch_spmv_tasks<float>(weighted, grid, st, a);
     if (c.kind == 1 && !heavy) {
 #define X(V, G) \
@@ -50,6 +64,14 @@ bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
 
 int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy)
 {
+    if (c.kind == 3) {
+        if (c.vec != 4 || c.nzl != 1) return 0;
+#define X(G) \
+    if (c.gs == G) return occupancy_async_cfg<G>(weighted, heavy);
+        RD_F32_ASYNC(X)
+#undef X
+        return 0;
+    }
     if (c.kind == 2 && !heavy) return occupancy_spmv_tasks<float>(weighted);
     if (c.kind == 1 && !heavy) {
 #define X(V, G) \
@@ -75,6 +97,9 @@ std::vector<SpmmCfg> spmm_configs_f32()
     v.push_back(SpmmCfg{1, 1, 1, 2});
 #define X(V, G) v.push_back(SpmmCfg{V, G, 1, 1});
     RD_F32_ROWS(X)
+#undef X
+#define X(G) v.push_back(SpmmCfg{4, G, 1, 3});
+    RD_F32_ASYNC(X)
 #undef X
     return v;
 }
