@@ -37,6 +37,10 @@ REL_TOL = 1e-6
 K_MAX = 200
 
 
+KERNEL_NAMES = {1: "k_spmm (+ k_spmm_heavy)", 2: "k_spmm_rows (+ k_spmm_heavy)", 3: "k_spmm, degree order",
+                4: "k_spmv_tasks", 5: "k_spmm_async (+ k_spmm_async_heavy)"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -52,17 +56,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def load_traffic(workload: str, launches_per_query: float):
-    """DRAM bytes per SpMM launch from the committed ncu summary, if it was taken on the
-    current kernel source, on this workload and over the same SpMM launches per query (the
-    mean is over that mix of widths), else None."""
+def load_traffic(workload: str, width: int):
+    """DRAM bytes of one SpMM launch pair (heavy-row pre-pass + main kernel) at the full width
+    of the profiled pass, from the committed ncu summary, if it was taken on the current kernel
+    source, on this workload and at this width, else None."""
     p = os.path.join(ROOT, "profiles", "spmm_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("kernel_source_sha1") != kernel_source_hash() or d.get("workload") != workload:
         return None
-    if d.get("spmm_launches_per_query") != round(launches_per_query):
+    if d.get("width") != width:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -177,14 +181,29 @@ def workload(rank: int, n: int = 1_000_000, pairs: int = 256):
     return g, s, t
 
 
+CPU_STOP = 1e-9    # relative increment at which the timed CPU baseline stops (stricter than 1e-6)
+REF_STOP = 1e-13   # relative increment of the oracle run that gives the reference values
+
+
 def cpu_oracle(g, s, t, sample: int, threads: int = 0):
+    """Timed CPU baseline: the oracle's -O3 build on `sample` pairs, one pair per thread."""
     from oracle import lanczos as O
 
-    O.build()
+    lib = O.load_timing()
     t0 = time.perf_counter()
-    r, k, used = O.lanczos_batch(g, s[:sample], t[:sample], k_max=K_MAX, stop_tol=1e-9, threads=threads)
+    r, k, used = O.lanczos_batch(g, s[:sample], t[:sample], k_max=K_MAX, stop_tol=CPU_STOP, threads=threads,
+                                 lib=lib)
     dt = time.perf_counter() - t0
     return r, k, used, dt
+
+
+def oracle_reference(g, s, t):
+    """Reference values for max_rel_err: the (pinned) oracle run to a relative increment of
+    1e-13 on every pair (untimed)."""
+    from oracle import lanczos as O
+
+    r, _, _ = O.lanczos_batch(g, s, t, k_max=K_MAX, stop_tol=REF_STOP, threads=0)
+    return r
 
 
 def host_info() -> dict:
@@ -229,8 +248,9 @@ def run_reference(args, world, rank):
         "config": {"workload": "chunglu1m_256pairs", "n": g.n, "nnz": g.nnz, "pairs_per_step": sample,
                    "sample": f"{sample} of the 256 pairs per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "host": host_info(),
+                         "build": "gcc -O3 -fopenmp",
                          "sample": f"{sample} pairs of the 256-pair workload per step, stop at relative "
-                                   f"increment 1e-9"},
+                                   f"increment {CPU_STOP:g}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -240,7 +260,8 @@ def run_reference(args, world, rank):
 def profile_config(rd, name, call="query"):
     """One SpMM-heavy query of a workload inside cudaProfilerStart/Stop, after a warm-up query
     (which also runs the autotuner), for ncu --profile-from-start off: 4 fixed Lanczos steps
-    over all of the workload's pairs (double-float vectors for the road grid). With
+    over all of the workload's pairs (double-float vectors for the road grid; for grid64 the
+    bench line's single-pair query: FP64, residual 1e-10, one whole-recurrence launch). With
     call="grad": instead the configs sweep's gradient call (rd_edge_grad over all of the
     workload's pairs, rel_tol 1e-6, k_max 200, upstream gradient 1), after a warm-up call."""
     import torch
@@ -253,7 +274,11 @@ def profile_config(rd, name, call="query"):
     G = rd.Graph.from_csr(g)
     sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
     mode = "df64" if name == "roadgrid4096" else "fp32"
-    if call == "grad":
+    if name == "grid64":  # the single-pair latency workload as the bench line runs it
+        mode = "fp64"
+        kw = dict(mode=mode, k_max=500, rel_tol=0.0, resid_tol=1e-10)
+        run = lambda: G.query(s, t, **kw)  # noqa: E731
+    elif call == "grad":
         ones = torch.ones(len(s), dtype=torch.float64, device="cuda")
         mode = "fp32"
         kw = dict(mode=mode, k_max=200, rel_tol=1e-6)
@@ -518,6 +543,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--plain-sample", type=int, default=16)
     ap.add_argument("--cpu1-sample", type=int, default=8, help="pairs of the one-core oracle timing")
+    ap.add_argument("--prof-steps", type=int, default=5,
+                    help="queries of the separate profiled pass that times the SpMM launches")
+    ap.add_argument("--profile-pass-range", action="store_true",
+                    help="bracket the first query of the profiled pass with cudaProfilerStart/Stop")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -580,14 +609,12 @@ def main():
     compactions = 0
     if args.profile_range:
         torch.cuda.profiler.start()
+    # the shipped configuration: CUDA-graph replay of the steps, no event timing inside
     e0.record(stream)
     for _ in range(args.steps):
-        res = G.query(s_dev, t_dev, profile=True, **opts)
+        res = G.query(s_dev, t_dev, **opts)
         st = G.last_stats()
         launches += st["launches"]
-        spmm_ms += st["spmm_ms"]
-        spmm_n += st["spmm_launches"]
-        spmm_bytes += st["spmm_bytes"]
         steps_max = max(steps_max, st["steps"])
         compactions += st["compactions"]
     e1.record(stream)
@@ -599,6 +626,22 @@ def main():
     ms = e0.elapsed_time(e1)
     ms_max = allmax(world, ms)
     value = job_throughput(P, world, args.steps, ms_max)
+    # a separate profiled pass gives the dominant kernel's launch times: the same query with
+    # CUDA events around every SpMM launch pair on the library's stream (launch-per-kernel
+    # loop) and without column compaction, so that every SpMM launch is the full-width one
+    # whose algorithmic bytes and DRAM traffic the roofline compares
+    for i in range(args.prof_steps):
+        if args.profile_pass_range and i == 0:
+            torch.cuda.profiler.start()
+        G.query(s_dev, t_dev, profile=True, compact=False, **opts)
+        if args.profile_pass_range and i == 0:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        sp = G.last_stats()
+        spmm_ms += sp["spmm_ms"]
+        spmm_n += sp["spmm_launches"]
+        spmm_bytes += sp["spmm_bytes"]
+    torch.cuda.synchronize()
     r_gpu = res.r.cpu().numpy()
     iters = res.iters.cpu().numpy()
     status = res.status.cpu().numpy()
@@ -612,8 +655,39 @@ def main():
     if not args.no_plain:
         plain_value, plain_r = run_plain(G, s_dev, t_dev, opts, args, stream)
     st["compactions_per_query"] = compactions / args.steps
+    st["grid64"] = run_grid64() if rank == 0 and not args.no_plain else None
     return finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st, launches, spmm_ms,
                   spmm_n, spmm_bytes, steps_max, clocks, e2e_value, plain_value, plain_r, s_np, t_np)
+
+
+def run_grid64(reps: int = 20) -> dict:
+    """The single-pair latency workload: 64x64 grid, corner to opposite corner, FP64, relative
+    residual 1e-10 (k <= 500), on the shipped path (the whole-recurrence kernel, here on a
+    thread-block cluster); error against the exact spectral sum."""
+    import torch
+
+    import paper_2601_11159_gb300 as rd
+    from graphgen import workloads as W
+    from tests import closed_forms as CF
+
+    g, s, t = W.grid64()
+    ref = CF.grid_r(64, 64, 0, 4095)
+    G = rd.Graph.from_csr(g)
+    kw = dict(mode="fp64", k_max=500, rel_tol=0.0, resid_tol=1e-10)
+    for _ in range(3):
+        r = G.query(s, t, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        r = G.query(s, t, **kw)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0) / reps
+    st = G.last_stats()
+    k = int(r.iters[0])
+    return {"workload": "grid64 corner pair (n = 4096), FP64, residual 1e-10", "ms_per_query": ms,
+            "steps": k, "us_per_step": 1e3 * ms / k, "rel_err_vs_closed_form": abs(float(r.r[0]) - ref) / ref,
+            "ctas_per_pair": int(st["onchip_ctas"]), "timing": f"host clock over {reps} queries (host ids in, "
+            "host result out)"}
 
 
 def run_e2e(G, s_np, t_np, opts, args, world):
@@ -663,22 +737,25 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
     avg_launch_ms = spmm_ms / max(spmm_n, 1)
     achieved = spmm_bytes / (spmm_ms / 1000.0) / 1e9 if spmm_n and spmm_ms > 0 else None
     workload_name = "chunglu1m_256pairs" if args.n == 1_000_000 and P == 256 else f"chunglu{args.n}_{P}pairs"
-    traffic = load_traffic(workload_name, spmm_n / max(args.steps, 1))
+    traffic = load_traffic(workload_name, P)
 
     cpu = None
     max_rel = None
     if not args.no_cpu:
         cs = min(args.cpu_sample, P)
         r_or, k_or, used, dt = cpu_oracle(g, s_np, t_np, cs)
-        rel = np.abs(r_gpu[:cs] - r_or) / np.abs(r_or)
+        r_ref = oracle_reference(g, s_np, t_np)
+        rel = np.abs(r_gpu - r_ref) / np.abs(r_ref)
         max_rel = float(rel.max())
         cpu = {"value": cs / dt, "unit": UNIT, "cores": int(used), "kind": "oracle", "host": host_info(),
-               "sample": f"{cs} of the {P} pairs, FP64 C Lanczos, stop at relative increment 1e-9; the same "
-                         f"run gives the reference values for max_rel_err",
+               "build": "gcc -O3 -fopenmp (no -march=native: host code builds alike on x86 and Arm)",
+               "sample": f"{cs} of the {P} pairs, FP64 C Lanczos, stop at relative increment {CPU_STOP:g}",
+               "reference": f"max_rel_err over all {P} pairs against the oracle run to a relative increment "
+                            f"of {REF_STOP:g}",
                "max_rel_err_gpu_vs_oracle": max_rel, "median_rel_err_gpu_vs_oracle": float(np.median(rel))}
         if plain_r is not None:
             ps = plain_r.size
-            cpu["max_rel_err_plain_vs_oracle"] = float((np.abs(plain_r - r_or[:ps]) / np.abs(r_or[:ps])).max())
+            cpu["max_rel_err_plain_vs_oracle"] = float((np.abs(plain_r - r_ref[:ps]) / np.abs(r_ref[:ps])).max())
         # one core (the paper's setting: one CPU thread), on a smaller sample of the same pairs
         _, _, _, dt1 = cpu_oracle(g, s_np, t_np, args.cpu1_sample, threads=1)
         cpu["single_core"] = {"value": args.cpu1_sample / dt1, "unit": UNIT, "cores": 1,
@@ -703,7 +780,12 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "k_spmm (+ k_spmm_heavy)", "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "kernel": KERNEL_NAMES.get(int(st["kernel"]), "spmm"),
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "timing": f"CUDA events around each SpMM launch pair on the library's stream, in a "
+                               f"separate profiled pass of {args.prof_steps} queries without column "
+                               f"compaction (every SpMM launch at the full {P}-column width); value and "
+                               f"e2e are timed on the CUDA-graph path without events",
                      "algorithmic_bytes_per_launch": spmm_bytes / max(spmm_n, 1), "avg_launch_ms": avg_launch_ms,
                      "launches_timed": spmm_n,
                      # DRAM bytes actually moved per launch (ncu, profiles/) over the live launch time
@@ -714,6 +796,7 @@ def finish(args, world, rank, g, P, value, ms_max, res, r_gpu, iters, status, st
         "cpu_baseline": cpu,
         "clocks": clocks,
         "max_rel_err": max_rel,
+        "single_pair_latency": st.get("grid64"),
     }
     print(json.dumps(line))
     return 0

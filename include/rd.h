@@ -114,6 +114,12 @@ typedef enum {
                                (p_i = q_i + (beta_i/delta_{i-1}) p_{i-1}, x += ||b|| (g_i/delta_i) p_i
                                from the LDL^T factors of I - T_i; one extra vector, no second pass);
                                the two agree to rounding */
+#define RD_Q_NO_CLUSTER 2048u /* rd_query: run the whole-recurrence kernel of small graphs with one CTA
+                               per pair. By default, when few pairs are asked (pairs x 2 x CTAs <= SMs),
+                               each pair's recurrence runs on a thread-block cluster of up to 16 CTAs
+                               (one per SM), each holding a slice of the three vectors in its shared
+                               memory and reading the others' through distributed shared memory; the
+                               two agree to rounding */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */
@@ -163,6 +169,8 @@ typedef struct {
     int32_t row_order;       /* 1 if the row-group kernel visited rows by decreasing degree */
     int32_t sparse_first;    /* 1 if the first step visited only the rows adjacent to s and t
                                 (see RD_Q_DENSE_FIRST) */
+    int32_t onchip_ctas;     /* CTAs per pair of the whole-recurrence kernel (1: one CTA, 2..16: a
+                                thread-block cluster; see RD_Q_NO_CLUSTER), 0 if it did not run */
 } rd_call_stats;
 
 /* Fill `opts` with defaults: k_max 1000, rel_tol 1e-7, resid_tol 0, FP32 vectors with FP64

@@ -22,14 +22,37 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False, src: str = _SRC, out: str = _SO) -> str:
+_SO_TIMING = os.path.join(_BUILD, "liboracle_O3.so")
+_lib_timing = None
+
+
+def build(force: bool = False, src: str = _SRC, out: str = _SO, opt: str = "-O2") -> str:
     """Compile the C oracle (plain -O2, OpenMP over pairs; no machine-specific flags)."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        subprocess.check_call(["gcc", opt, "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
         os.replace(tmp, out)
     return out
+
+
+def build_timing(force: bool = False) -> str:
+    """The same source compiled with -O3 for the timed CPU baseline (the pinned build used by
+    the tests stays -O2). No -march=native: host code here must build and give the same
+    results on the x86 and Arm hosts, and -O3 alone already vectorises for the baseline ISA
+    of each."""
+    return build(force, _SRC, _SO_TIMING, "-O3")
+
+
+def load_timing():
+    """The -O3 build of the oracle (see build_timing), for timing only."""
+    global _lib_timing
+    if _lib_timing is None:
+        lib = load(build_timing())  # load() takes the module lock itself
+        with _lock:
+            if _lib_timing is None:
+                _lib_timing = lib
+    return _lib_timing
 
 
 def load(path: str = None):

@@ -43,6 +43,7 @@ RD_Q_NO_GRAPH = 128
 RD_Q_EST_DELAYED = 256
 RD_Q_DENSE_FIRST = 512
 RD_Q_REPLAY_POTENTIAL = 1024
+RD_Q_NO_CLUSTER = 2048
 
 
 class QueryOpts(C.Structure):
@@ -75,6 +76,7 @@ class CallStats(C.Structure):
         ("tuned", C.c_int32),
         ("row_order", C.c_int32),
         ("sparse_first", C.c_int32),
+        ("onchip_ctas", C.c_int32),
     ]
 
 

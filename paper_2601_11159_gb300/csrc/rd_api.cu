@@ -615,7 +615,8 @@ struct RunCtx {
     int cf_sel = 0, slot_sel = -1;  // slot_sel < 0: identity slot map
     bool in_region_x = false;
     bool lazy_walk = false;  // Power Method steps instead of Lanczos steps
-    bool onchip = false;     // whole recurrence per pair in one CTA (small graphs, queries only)
+    bool onchip = false;     // whole recurrence per pair in one kernel (small graphs, queries only)
+    int onchip_ctas = 0;     // CTAs per pair it ran with (1, or a cluster of 2..16)
     bool graph = false;      // steps replayed from a captured CUDA graph of one step
     bool sparse_first = false;  // first step run by k_step0_sparse
     bool pot_x = false;      // potential accumulated during the forward steps (k_normalize_pot)
@@ -715,8 +716,7 @@ static rd_status enqueue_spmm(RunCtx& c, int j, bool reduce)
         if (!launch_spmm_t(c.cur.cfg, c.g->weighted, true, c.cur.grid_heavy, c.st, a)) return RD_ERR_UNSUPPORTED;
         ++c.launches;
     }
-    bool ok = launch_spmm_t(c.cur.cfg, c.g->weighted, false, c.cur.grid_main, c.st, a);
-    if (!ok) return RD_ERR_UNSUPPORTED;
+    if (!launch_spmm_t(c.cur.cfg, c.g->weighted, false, c.cur.grid_main, c.st, a)) return RD_ERR_UNSUPPORTED;
     ++c.launches;
     ++c.spmm_launches;
     c.spmm_bytes += spmm_launch_bytes(c.g, c.cur);
@@ -996,6 +996,7 @@ static rd_status run_forward(RunCtx& c)
     fa.resid_tol = c.o.resid_tol;
     fa.est_delayed = (c.o.flags & RD_Q_EST_DELAYED) ? 1 : 0;
     fa.sumdeg = c.g->sumdeg;
+    fa.inv_sumdeg = c.g->sumdeg > 0.0 ? 1.0 / c.g->sumdeg : 0.0;
     fa.block_part = c.b.block_part;
     fa.st = c.b.st;
     fa.elem_size = (int)c.pl.elem;
@@ -1029,7 +1030,11 @@ static rd_status run_forward(RunCtx& c)
         oa.fin = fa;
         oa.elem_size = (int)c.pl.elem;
         oa.weighted = c.g->weighted ? 1 : 0;
-        if (launch_onchip(c.st, oa)) {
+        oa.sm_count = c.g->sm_count;
+        oa.allow_cluster = (c.o.flags & RD_Q_NO_CLUSTER) ? 0 : 1;
+        const int ctas = launch_onchip(c.st, oa);
+        if (ctas > 0) {
+            c.onchip_ctas = ctas;
             ++c.launches;
             RD_CUDA(cudaGetLastError());
             return RD_OK;
@@ -1152,6 +1157,7 @@ static void record_stats(RunCtx& c)
     s.tuned = c.pl.tuned ? 1 : 0;
     s.row_order = c.pl.cfg.order;
     s.sparse_first = c.sparse_first ? 1 : 0;
+    s.onchip_ctas = c.onchip_ctas;
     if (c.profile) {
         double ms = 0.0;
         for (auto& pr : c.spmm_ev) {
@@ -1241,6 +1247,7 @@ static std::vector<SpmmCfg> tune_candidates(const rd_graph* g, int64_t width, bo
     }
     // async row-stream (FP32 vectors): column slabs of 16 to 128 columns, down to an eighth
     // of the width (narrow slabs keep the gathered slab in L2)
+    // async row-stream (FP32 vectors): column slabs of 16 to 128 columns
     if (!fp64)
         for (int64_t tp = std::max<int64_t>(16, width / 8); tp <= std::min<int64_t>(width, 128); tp <<= 1)
             add(4, (int)(tp / 4), 1, 3, 0);

@@ -162,6 +162,7 @@ struct FinArgs {
     int npairs, tp, nblocks, step;      // step: 0-based index of the step just reduced
     int k_max, deflate, fixed_k, fp64;
     double rel_tol, resid_tol, sumdeg;
+    double inv_sumdeg;                  // 1 / sumdeg
     int est_delayed;                    // 1: delayed-sum error estimate (RD_Q_EST_DELAYED)
     const double* block_part;
     PairState st;
@@ -196,9 +197,13 @@ struct OnchipArgs {
     const int32_t* heavy_rows;
     FinArgs fin;                  // stop rule, tolerances, per-pair state
     int elem_size, weighted;
+    int sm_count;                 // SMs of the device (cluster size choice)
+    int allow_cluster;            // 0: one CTA per pair (RD_Q_NO_CLUSTER)
 };
 size_t onchip_smem_bytes(int64_t n, int elem_size);
-bool launch_onchip(cudaStream_t st, const OnchipArgs& a);
+// Launches the whole-recurrence kernel; returns the CTAs per pair used (1: one CTA per pair,
+// 2..16: a thread-block cluster per pair), or 0 if the graph does not fit.
+int launch_onchip(cudaStream_t st, const OnchipArgs& a);
 
 // Column compaction: keep the slots whose pair is still active, in slot order.
 struct CompactArgs {
@@ -275,6 +280,7 @@ struct rd_graph {
     int32_t* row_order = nullptr;
     // row of every stored entry (built on first use by the per-entry kernels)
     int32_t* entry_row = nullptr;
+
     bool rows_sorted_sym = false;     // rows strictly increasing in column, entries symmetric
     double mean_deg = 0.0;
     rd::Workspace ws;
@@ -371,6 +377,7 @@ struct EdgeGradArgs {
 void launch_edge_grad_f32(int grid, cudaStream_t st, const EdgeGradArgs<float>& a);
 void launch_edge_grad_f64(int grid, cudaStream_t st, const EdgeGradArgs<double>& a);
 void launch_entry_rows(int grid, cudaStream_t st, int64_t n, const int64_t* row_ptr, int32_t* entry_row);
+
 
 // First Lanczos step from the sparse start vector (two nonzeros per column).
 template <typename T>

@@ -5,6 +5,8 @@
 // potential of Algorithm 5 and the edge-weight gradient.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "spmm.cuh"
 
 namespace rd {
@@ -86,13 +88,60 @@ void launch_init(cudaStream_t st, const InitArgs& a)
 //   residual ||b - (I - Ahat) x_i||/||b|| = beta_{i+1} |g_i/delta_i|.
 // Writes the pair's state and history; returns true when the pair stops (then active = 0),
 // else leaves alpha_i, the deflation constant c_i and beta_{i+1} in the outputs.
-__device__ __forceinline__ bool pair_update(const FinArgs& a, const PairState& st, int p, int j, double A, double B,
-                                            double C, double* alpha_o, double* cdef_o, double* beta_next_o)
+// The per-pair scalars of the update (a register copy of one pair's PairState entries).
+struct PairScalars {
+    double b2, delta, g, S, beta;  // beta: beta_i of the step being reduced
+    double inv_delta;              // 1 / delta (0 before the first step)
+    double r0, r1, r2, r3;         // increments of S: slot j % kRing holds step j's
+    // slot access by a run-time index through selects, so that the scalars stay in registers
+    // (an indexed array would live in local memory)
+    __device__ __forceinline__ double ring(int q) const { return q == 0 ? r0 : (q == 1 ? r1 : (q == 2 ? r2 : r3)); }
+    __device__ __forceinline__ void set_ring(int q, double v)
+    {
+        r0 = q == 0 ? v : r0;
+        r1 = q == 1 ? v : r1;
+        r2 = q == 2 ? v : r2;
+        r3 = q == 3 ? v : r3;
+    }
+};
+static_assert(kRing == 4, "PairScalars holds four ring slots");
+
+// What one step produced (the values pair_update stores).
+struct PairStepOut {
+    bool ok;                       // false: a value was not finite or I - T_i lost definiteness
+    bool warn_not_converged;       // k_max reached before a tolerance was met
+    double alpha, cdef, beta_next, incr, r, resid, est;
+};
+
+__device__ __forceinline__ PairScalars pair_load(const PairState& st, int p, int64_t np)
 {
-    const int64_t np = a.pstride;  // stride of the per-pair arrays
+    PairScalars s;
+    s.b2 = st.b2[p];
+    s.delta = st.delta[p];
+    s.g = st.g[p];
+    s.S = st.S[p];
+    s.beta = st.beta[p];
+    s.inv_delta = s.delta != 0.0 ? 1.0 / s.delta : 0.0;
+    s.r0 = st.ring[p];
+    s.r1 = st.ring[np + p];
+    s.r2 = st.ring[2 * np + p];
+    s.r3 = st.ring[3 * np + p];
+    return s;
+}
+
+// The arithmetic of one step on the scalars (see pair_update); returns true when the pair
+// stops. The state in `s` is advanced exactly as pair_update advances the stored state.
+// FP64 division and square root are slow on this part (hundreds of cycles each, one thread
+// at a time on the whole-recurrence kernels' critical path), so the step takes four divisions
+// and one square root: 1/delta_{i-1} is kept from the previous step, 1/sum(d) is passed in,
+// 1/delta_i and 1/S_i serve every quotient by them, and the largest increment ratio is found
+// by cross-multiplication (increments are positive) before its one division.
+__device__ __forceinline__ bool pair_core(const FinArgs& a, PairScalars& s, int j, double A, double B, double C,
+                                          PairStepOut& o)
+{
     const double alpha = A;
-    const double beta_i = st.beta[p];
-    const double cdef = a.deflate ? C / a.sumdeg : 0.0;
+    const double beta_i = s.beta;
+    const double cdef = a.deflate ? C * a.inv_sumdeg : 0.0;
     const double gamma2 = a.deflate ? C * cdef : 0.0;
     const double beta2 = B - alpha * alpha - gamma2;
     double delta, g;
@@ -100,70 +149,109 @@ __device__ __forceinline__ bool pair_update(const FinArgs& a, const PairState& s
         delta = 1.0 - alpha;
         g = 1.0;
     } else {
-        const double dprev = st.delta[p];
-        delta = (1.0 - alpha) - beta_i * beta_i / dprev;
-        g = st.g[p] * beta_i / dprev;
+        const double idp = s.inv_delta;
+        delta = (1.0 - alpha) - beta_i * beta_i * idp;
+        g = s.g * beta_i * idp;
     }
     bool stop = false;
-    const bool ok = isfinite(alpha) && isfinite(beta2) && isfinite(delta) && delta > 0.0;
-    double beta_next = 0.0;
-    if (!ok) {
-        st.status[p] = RD_ERR_NUMERIC;  // frozen at its last good estimate
-        stop = true;
-    } else {
-        const double incr = g * g / delta;
-        const double S = st.S[p] + incr;
-        st.S[p] = S;
-        st.r[p] = st.b2[p] * S;
-        st.ring[(int64_t)(j % kRing) * np + p] = incr;
-        beta_next = sqrt(fmax(beta2, 0.0));
-        const double resid = beta_next * fabs(g / delta);
-        st.resid[p] = resid;
-        // Relative error estimate of r_k = b2 * S_k: the increments still to come. Default:
-        // their sum as a series whose ratio is the largest of the last kRing-1 increment
-        // ratios (at least 1/2), with an extra margin 1/(1 - rho) for slowly converging
-        // pairs: incr * rho / (1 - rho)^2. Alternative (est_delayed): the sum of the last
-        // kRing increments, i.e. the error of the estimate kRing steps back.
+    o.ok = isfinite(alpha) && isfinite(beta2) && isfinite(delta) && delta > 0.0;
+    o.warn_not_converged = false;
+    o.alpha = alpha;
+    o.cdef = cdef;
+    o.beta_next = 0.0;
+    if (!o.ok) return true;  // frozen at its last good estimate
+    const double inv_delta = 1.0 / delta;
+    const double gd = g * inv_delta;
+    const double incr = g * gd;
+    const double S = s.S + incr;
+    s.S = S;
+    o.incr = incr;
+    o.r = s.b2 * S;
+    s.set_ring(j % kRing, incr);
+    const double beta_next = sqrt(fmax(beta2, 0.0));
+    o.beta_next = beta_next;
+    const double resid = beta_next * fabs(gd);
+    o.resid = resid;
+    s.delta = delta;
+    s.inv_delta = inv_delta;
+    s.g = g;
+    const double brk = a.fp64 ? 1e-12 : 1e-6;
+    const bool breakdown = beta_next <= brk * (fabs(alpha) + beta_i);  // T_i is exact
+    stop = breakdown || (!a.fixed_k && a.resid_tol > 0.0 && resid <= a.resid_tol);
+    // Relative error estimate of r_k = b2 * S_k: the increments still to come. Default:
+    // their sum as a series whose ratio is the largest of the last kRing-1 increment
+    // ratios (at least 1/2), with an extra margin 1/(1 - rho) for slowly converging
+    // pairs: incr * rho / (1 - rho)^2. Alternative (est_delayed): the sum of the last
+    // kRing increments, i.e. the error of the estimate kRing steps back. Without a rel_tol
+    // test it only feeds the output, so it is formed on the step that ends the pair.
+    const bool use_est = !a.fixed_k && a.rel_tol > 0.0;
+    double est = 0.0;
+    if (!breakdown && (use_est || stop || j + 1 >= a.k_max)) {
+        const double inv_S = 1.0 / S;
         double tail = 0.0;
         const int nr = j + 1 < kRing ? j + 1 : kRing;
-        for (int q = 0; q < nr; ++q) tail += st.ring[(int64_t)q * np + p];
-        double est = tail / S;
+        for (int q = 0; q < nr; ++q) tail += s.ring(q);
+        est = tail * inv_S;
         if (!a.est_delayed && j + 1 >= kRing) {
-            double rho = 0.5;
-            for (int q = 1; q < kRing; ++q) {
-                const double num = st.ring[(int64_t)((j - q + 1) % kRing) * np + p];
-                const double den = st.ring[(int64_t)((j - q) % kRing) * np + p];
-                rho = fmax(rho, num / den);
+            // the largest num/den over the last kRing-1 pairs of consecutive increments
+            double bn = s.ring(j % kRing), bd = s.ring((j - 1) % kRing);
+            for (int q = 2; q < kRing; ++q) {
+                const double num = s.ring((j - q + 1) % kRing);
+                const double den = s.ring((j - q) % kRing);
+                if (num * bd > bn * den) {
+                    bn = num;
+                    bd = den;
+                }
             }
-            est = rho < 1.0 ? incr * rho / ((1.0 - rho) * (1.0 - rho)) / S : INFINITY;
+            const double rho = fmax(0.5, bn / bd);
+            const double om = 1.0 - rho;
+            est = rho < 1.0 ? incr * rho * inv_S / (om * om) : INFINITY;
         }
-        st.err[p] = est;
-        st.hist_alpha[(int64_t)j * np + p] = alpha;
-        st.hist_beta[(int64_t)(j + 1) * np + p] = beta_next;
+        if (!stop && use_est && j + 1 >= kRing && est <= a.rel_tol) stop = true;
+    }
+    o.est = est;
+    if (!stop && j + 1 >= a.k_max) {
+        stop = true;
+        o.warn_not_converged = !a.fixed_k;
+    }
+    if (!stop) s.beta = beta_next;
+    return stop;
+}
+
+// Store one step's results of pair p (the history, the running factorisation, the status).
+__device__ __forceinline__ void pair_store(const PairState& st, int p, int j, int64_t np, const PairScalars& s,
+                                           const PairStepOut& o, bool stop)
+{
+    if (!o.ok) {
+        st.status[p] = RD_ERR_NUMERIC;
+    } else {
+        st.S[p] = s.S;
+        st.r[p] = o.r;
+        st.ring[(int64_t)(j % kRing) * np + p] = o.incr;
+        st.resid[p] = o.resid;
+        st.err[p] = o.est;
+        st.hist_alpha[(int64_t)j * np + p] = o.alpha;
+        st.hist_beta[(int64_t)(j + 1) * np + p] = o.beta_next;
         st.k[p] = j + 1;
-        st.delta[p] = delta;
-        st.g[p] = g;
-        const double brk = a.fp64 ? 1e-12 : 1e-6;
-        if (beta_next <= brk * (fabs(alpha) + beta_i)) {
-            stop = true;  // Krylov space exhausted: T_i is exact
-            st.err[p] = 0.0;
-        } else if (!a.fixed_k) {
-            if (a.resid_tol > 0.0 && resid <= a.resid_tol) stop = true;
-            if (a.rel_tol > 0.0 && j + 1 >= kRing && est <= a.rel_tol) stop = true;
-        }
-        if (!stop && j + 1 >= a.k_max) {
-            stop = true;
-            if (!a.fixed_k) st.status[p] = RD_WARN_NOT_CONVERGED;
-        }
+        st.delta[p] = s.delta;
+        st.g[p] = s.g;
+        if (o.warn_not_converged) st.status[p] = RD_WARN_NOT_CONVERGED;
     }
-    if (stop) {
-        st.active[p] = 0;
-        return true;
-    }
-    st.beta[p] = beta_next;
-    *alpha_o = alpha;
-    *cdef_o = cdef;
-    *beta_next_o = beta_next;
+    if (stop) st.active[p] = 0;
+    else st.beta[p] = s.beta;
+}
+
+__device__ __forceinline__ bool pair_update(const FinArgs& a, const PairState& st, int p, int j, double A, double B,
+                                            double C, double* alpha_o, double* cdef_o, double* beta_next_o)
+{
+    PairScalars s = pair_load(st, p, a.pstride);
+    PairStepOut o;
+    const bool stop = pair_core(a, s, j, A, B, C, o);
+    pair_store(st, p, j, a.pstride, s, o, stop);
+    if (stop) return true;
+    *alpha_o = o.alpha;
+    *cdef_o = o.cdef;
+    *beta_next_o = o.beta_next;
     return false;
 }
 
@@ -947,10 +1035,235 @@ __global__ void __launch_bounds__(kOnchipThreads) k_lanczos_onchip(const OnchipA
     }
 }
 
-bool launch_onchip(cudaStream_t st, const OnchipArgs& a)
+// ---------------------------------------------------- on chip, one cluster per pair
+// The same recurrence for one pair spread over a thread-block cluster of C CTAs (C = 2..16):
+// CTA r holds rows [r R, (r+1) R) of q_{i-1}, q_i and W in its shared memory (R a power of
+// two), and the product gathers q_i[col] from the owning CTA's shared memory through the
+// cluster's distributed shared memory. Per step: every CTA's three FP64 block sums are
+// written into every CTA of the cluster, a cluster barrier, every CTA sums the C partials in
+// rank order and runs the same scalar update (pair_core) on its own copy of the pair's
+// scalars (identical inputs, identical results; rank 0 also stores them), normalises its
+// rows in place, and a second cluster barrier publishes the new vector. The FP64 work of a
+// step is spread over C SMs (one CTA per SM) instead of one.
+constexpr int kClusterThreads = 256;
+constexpr int kClusterMax = 16;
+
+struct ClusterLayout {
+    int shift;        // log2 R: rows per CTA
+    int C;            // CTAs per pair
+};
+
+template <typename T, bool WEIGHTED>
+__global__ void __launch_bounds__(kClusterThreads) k_lanczos_cluster(const OnchipArgs a, const ClusterLayout L)
 {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char cl_raw[];
+    __shared__ double part[kClusterMax][3];
+    __shared__ double tpart[3][kClusterThreads];  // per-thread partial sums of the step
+    __shared__ double coef[3];
+    __shared__ int stop_s;
+    __shared__ T* rbase[3][kClusterMax];  // generic addresses of every rank's buffers
+    const int C = L.C;
+    const int rank = (int)cluster.block_rank();
+    const int p = blockIdx.x / C;
+    const PairState& st = a.fin.st;
+    // uniform over the cluster: no CTA changes active[p] before the first cluster barrier
+    if (p >= a.npairs || !st.active[p]) return;
+    const int64_t n = a.n;
+    const int64_t R = (int64_t)1 << L.shift;
+    const int64_t row0 = (int64_t)rank * R;
+    const int64_t nrow = row0 >= n ? 0 : (n - row0 < R ? n - row0 : R);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nthr = kClusterThreads, nwarps = kClusterThreads / 32;
+    T* buf0 = reinterpret_cast<T*>(cl_raw);
+    if (tid < 3 * C) {
+        const int b = tid / C, rr = tid % C;
+        rbase[b][rr] = cluster.map_shared_rank(buf0 + b * R, rr);
+    }
+    for (int64_t u = tid; u < 3 * R; u += nthr) buf0[u] = T(0);
+    __syncthreads();
+    PairScalars ps;
+    if (tid == 0) {
+        ps = pair_load(st, p, a.fin.pstride);
+        const int32_t s = a.s[p], t = a.t[p];
+        const double bn = sqrt(ps.b2);
+        if (s >= row0 && s < row0 + nrow) buf0[R + (s - row0)] = (T)(1.0 / (a.deg64[s] * bn));
+        if (t >= row0 && t < row0 + nrow) buf0[R + (t - row0)] = (T)(-1.0 / (a.deg64[t] * bn));
+    }
+    cluster.sync();  // every slice of q_1 is in place
+    int iprev = 0, icur = 1, iw = 2;
+    const int64_t mask = R - 1;
+    T bt = T(0);
+    for (int j = 0; j < a.fin.k_max; ++j) {
+        T* const* cur = rbase[icur];
+        const T* qp = buf0 + iprev * R;
+        const T* qc = buf0 + icur * R;
+        T* W = buf0 + iw * R;
+        double pa = 0.0, pb = 0.0, pc = 0.0;
+        for (int64_t ul = tid; ul < nrow; ul += nthr) {
+            const int64_t u = row0 + ul;
+            const int64_t e0 = a.row_ptr[u], e1 = a.row_ptr[u + 1];
+            if (e1 - e0 > a.heavy_thr) continue;
+            T acc = T(0);
+            for (int64_t e = e0; e < e1; ++e) {
+                const int32_t v = __ldg(a.col + e);
+                const T x = cur[v >> L.shift][v & mask];
+                if constexpr (WEIGHTED) acc += (T)__ldg(a.w + e) * x;
+                else acc += x;
+            }
+            const T invd = sizeof(T) == 8 ? (T)a.invdeg64[u] : (T)a.invdeg32[u];
+            const T du = sizeof(T) == 8 ? (T)a.deg64[u] : (T)a.deg32[u];
+            const T wv = invd * acc - bt * qp[ul];
+            W[ul] = wv;
+            const T dw = du * wv;
+            pa += (double)(dw * qc[ul]);
+            pb += (double)(dw * wv);
+            pc += (double)dw;
+        }
+        for (int64_t h = warp; h < a.n_heavy_rows; h += nwarps) {
+            const int64_t u = a.heavy_rows[h];
+            if (u < row0 || u >= row0 + nrow) continue;
+            T acc = T(0);
+            for (int64_t e = a.row_ptr[u] + lane; e < a.row_ptr[u + 1]; e += 32) {
+                const int32_t v = __ldg(a.col + e);
+                const T x = cur[v >> L.shift][v & mask];
+                if constexpr (WEIGHTED) acc += (T)__ldg(a.w + e) * x;
+                else acc += x;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += shfl_xor_t(0xffffffffu, acc, off);
+            if (lane == 0) {
+                const int64_t ul = u - row0;
+                const T invd = sizeof(T) == 8 ? (T)a.invdeg64[u] : (T)a.invdeg32[u];
+                const T du = sizeof(T) == 8 ? (T)a.deg64[u] : (T)a.deg32[u];
+                const T wv = invd * acc - bt * qp[ul];
+                W[ul] = wv;
+                const T dw = du * wv;
+                pa += (double)(dw * qc[ul]);
+                pb += (double)(dw * wv);
+                pc += (double)dw;
+            }
+        }
+        // the CTA's three sums by one warp (FP64 adds are slow here, and the shuffles of the
+        // other warps would contend for the same units): lane l adds threads l, l+32, ... in
+        // order, then a fixed xor tree; lane r < C writes them into slot `rank` of CTA r
+        tpart[0][tid] = pa;
+        tpart[1][tid] = pb;
+        tpart[2][tid] = pc;
+        __syncthreads();
+        if (warp == 0) {
+            double A = 0.0, B = 0.0, Cs = 0.0;
+            for (int w = 0; w < nwarps; ++w) {
+                A += tpart[0][w * 32 + lane];
+                B += tpart[1][w * 32 + lane];
+                Cs += tpart[2][w * 32 + lane];
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                A += __shfl_xor_sync(0xffffffffu, A, off);
+                B += __shfl_xor_sync(0xffffffffu, B, off);
+                Cs += __shfl_xor_sync(0xffffffffu, Cs, off);
+            }
+            if (lane < C) {
+                double* dst = cluster.map_shared_rank(&part[0][0], lane);
+                dst[rank * 3 + 0] = A;
+                dst[rank * 3 + 1] = B;
+                dst[rank * 3 + 2] = Cs;
+            }
+        }
+        cluster.sync();  // all partial sums have arrived
+        if (tid == 0) {
+            double A = 0.0, B = 0.0, Cs = 0.0;
+            for (int rr = 0; rr < C; ++rr) {
+                A += part[rr][0];
+                B += part[rr][1];
+                Cs += part[rr][2];
+            }
+            PairStepOut o;
+            const bool stop = pair_core(a.fin, ps, j, A, B, Cs, o);
+            if (rank == 0) pair_store(st, p, j, a.fin.pstride, ps, o, stop);
+            stop_s = stop ? 1 : 0;
+            coef[0] = o.alpha;
+            coef[1] = o.cdef;
+            coef[2] = o.beta_next;
+        }
+        __syncthreads();
+        if (stop_s) break;  // the same decision in every CTA of the cluster
+        const T al = (T)coef[0], cd = (T)coef[1], ib = (T)(1.0 / coef[2]);
+        for (int64_t ul = tid; ul < nrow; ul += nthr) W[ul] = (W[ul] - al * qc[ul] - cd) * ib;
+        bt = (T)coef[2];
+        const int old_prev = iprev;
+        iprev = icur;
+        icur = iw;
+        iw = old_prev;
+        cluster.sync();  // the new q_i is complete in every CTA before the next product reads it
+    }
+    cluster.sync();  // no CTA leaves while another may still address its shared memory
+}
+
+// Cluster size for the whole-recurrence kernel: as many CTAs per pair as keep every pair's
+// cluster resident at once (npairs * C <= SMs), at least 32 rows per CTA, at most 16; 1 when
+// a cluster would not help (the single-CTA kernel then runs).
+static int cluster_size(const OnchipArgs& a)
+{
+    if (!a.allow_cluster || a.n_heavy_rows > 64) return 1;
+    int C = 1;
+    while (C < kClusterMax && (int64_t)a.npairs * C * 2 <= a.sm_count && a.n >= (int64_t)64 * C) C <<= 1;
+    return C;
+}
+
+template <typename T, bool WEIGHTED>
+static int launch_cluster_t(cudaStream_t st, const OnchipArgs& a, int C)
+{
+    auto k = k_lanczos_cluster<T, WEIGHTED>;
+    ClusterLayout L;
+    L.C = C;
+    const int64_t rows = (a.n + C - 1) / C;
+    L.shift = 0;
+    while (((int64_t)1 << L.shift) < rows) ++L.shift;
+    // three row blocks, but at least 120 KB so that one CTA of the cluster occupies an SM (the
+    // FP64 rate per SM is what a cluster multiplies)
+    const size_t need = (size_t)3 * ((size_t)1 << L.shift) * sizeof(T);
+    if (need > 200 * 1024) return 0;
+    const size_t sm = need < 120 * 1024 ? 120 * 1024 : need;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
+    if (C > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(a.npairs * C), 1, 1);
+    cfg.blockDim = dim3(kClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaLaunchKernelEx(&cfg, k, a, L) != cudaSuccess) {
+        cudaGetLastError();  // a refused configuration is not sticky: try a smaller cluster
+        return 0;
+    }
+    return C;
+}
+
+int launch_onchip(cudaStream_t st, const OnchipArgs& a)
+{
+    for (int C = cluster_size(a); C > 1; C >>= 1) {
+        int used = 0;
+        if (a.elem_size == 8) used = a.weighted ? launch_cluster_t<double, true>(st, a, C)
+                                                : launch_cluster_t<double, false>(st, a, C);
+        else used = a.weighted ? launch_cluster_t<float, true>(st, a, C) : launch_cluster_t<float, false>(st, a, C);
+        if (used) return used;
+    }
     const size_t sm = onchip_smem_bytes(a.n, a.elem_size);
-    if (sm > 220 * 1024) return false;
+    if (sm > 220 * 1024) return 0;
     if (a.elem_size == 8) {
         auto k = a.weighted ? k_lanczos_onchip<double, true> : k_lanczos_onchip<double, false>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -960,7 +1273,7 @@ bool launch_onchip(cudaStream_t st, const OnchipArgs& a)
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k<<<a.npairs, kOnchipThreads, sm, st>>>(a);
     }
-    return true;
+    return 1;
 }
 
 }  // namespace rd

@@ -134,7 +134,7 @@ def test_header_constants_match_the_binding():
 
 def test_bench_uses_the_traffic_summary_only_where_it_was_taken():
     """bench.py reports the committed ncu DRAM traffic only for the kernel source, workload and
-    SpMM launches per query it was captured on."""
+    launch width it was captured on."""
     import json
     import sys
 
@@ -142,9 +142,9 @@ def test_bench_uses_the_traffic_summary_only_where_it_was_taken():
     import bench
 
     d = json.load(open(os.path.join(ROOT, "profiles", "spmm_traffic.json")))
-    n = d["spmm_launches_per_query"]
+    w = d["width"]
     same_source = d["kernel_source_sha1"] == bench.kernel_source_hash()
-    got = bench.load_traffic(d["workload"], n)
+    got = bench.load_traffic(d["workload"], w)
     assert got == (d["dram_bytes_per_launch"] if same_source else None)
-    assert bench.load_traffic(d["workload"], n + 1) is None
-    assert bench.load_traffic("chunglu1000000_128pairs", n) is None
+    assert bench.load_traffic(d["workload"], w // 2) is None
+    assert bench.load_traffic("chunglu1000000_128pairs", w) is None

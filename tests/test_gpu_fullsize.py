@@ -79,6 +79,66 @@ def test_roadgrid4096_fp64(rd):
     assert rel(back.r, res.r[:1]).max() < 1e-6
 
 
+def test_grid4096_unit_converged_vs_closed_form(rd, capsys):
+    """Large-kappa parity at full size against an exact reference: the undeleted unit-weight
+    4096^2 grid (kappa ~ 1.4e7, the road-grid workload before deletion and weighting), 8 pairs
+    at Manhattan distance 1000, run to relative residual 1e-10 in FP64 and in double-float
+    vectors, against the exact spectral sum (an O(N^2) FP64 sum per pair) at 1e-9 relative.
+    The FP32-vector path is run too and stays within its documented floor (about 2e-4 at
+    this kappa)."""
+    g = F.grid(4096)
+    s, t = F.grid_distance_pairs(g, 8, 1000, 13)
+    ref = np.array([CF.grid_r(4096, 4096, int(a), int(b)) for a, b in zip(s, t)])
+    G = rd.Graph.from_csr(g)
+    errs = {}
+    for mode in ("fp64", "df64"):
+        res = G.query(s, t, mode=mode, k_max=60000, rel_tol=0.0, resid_tol=1e-10)
+        assert np.all(res.status == 0), (mode, np.unique(res.status))
+        errs[mode] = (rel(res.r, ref).max(), int(res.iters.max()))
+        assert errs[mode][0] < FP64_TOL, (mode, errs[mode])
+    r32 = G.query(s, t, mode="fp32", k_max=60000, rel_tol=0.0, resid_tol=1e-6)
+    errs["fp32"] = (rel(r32.r, ref).max(), int(r32.iters.max()))
+    assert errs["fp32"][0] < 1e-3, errs["fp32"]
+    with capsys.disabled():
+        print(f"\ngrid4096 unit, 8 pairs at distance 1000: max rel. error / steps {errs}")
+
+
+def test_roadgrid1024_converged_vs_oracle(rd, capsys):
+    """Converged parity on a road-like grid small enough for the CPU oracle: 1024^2, 5% of the
+    edges deleted, weights U[0.5, 2] (kappa ~ 1e6), 8 pairs at distance 256, against the FP64
+    oracle run to a 1e-13 relative increment (stored by tests/golden/make_roadgrid1024_ref.py,
+    which also checks two of the pairs against Jacobi-CG to 1e-9). FP64 and double-float
+    vectors to relative residual 1e-12 within 1e-9; FP32 vectors within 1e-3 (their floor)."""
+    import json
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_roadgrid1024_ref as M
+
+    ref_doc = json.load(open(M.OUT))
+    g, s, t = M.graph_and_pairs()
+    assert M.checksum(g) == ref_doc["graph"]["sha1"], "the generator no longer makes the stored graph"
+    assert s.tolist() == ref_doc["pairs"]["s"] and t.tolist() == ref_doc["pairs"]["t"]
+    ref = np.array(ref_doc["oracle"]["r"])
+    G = rd.Graph.from_csr(g)
+    errs = {}
+    for mode in ("fp64", "df64"):
+        res = G.query(s, t, mode=mode, k_max=60000, rel_tol=0.0, resid_tol=1e-12)
+        assert np.all(res.status == 0), (mode, np.unique(res.status))
+        errs[mode] = (rel(res.r, ref).max(), int(res.iters.max()))
+        assert errs[mode][0] < FP64_TOL, (mode, errs[mode])
+    for mode, kw in (("fp32", dict(rel_tol=0.0, resid_tol=1e-6)), ("fp32 rel_tol 1e-6", dict(rel_tol=1e-6))):
+        r32 = G.query(s, t, mode="fp32", k_max=60000, **kw)
+        errs[mode] = (rel(r32.r, ref).max(), int(r32.iters.max()))
+        assert errs[mode][0] < 1e-3, (mode, errs[mode])
+    res = G.query(s, t, mode="df64", k_max=60000, rel_tol=1e-6)
+    errs["df64 rel_tol 1e-6"] = (rel(res.r, ref).max(), int(res.iters.max()))
+    assert errs["df64 rel_tol 1e-6"][0] < 1e-5
+    with capsys.disabled():
+        print(f"\nroadgrid1024, 8 pairs at distance 256: max rel. error / steps {errs}")
+
+
 def test_chunglu4m_weighted_gradient(rd):
     """Chung-Lu n=4M, exponent 2.3, lognormal(0, 0.5) weights, 32 pairs: r on sampled pairs
     (FP32 and FP64); the edge gradient against (i) the oracle's potential gradient on sampled

@@ -188,16 +188,19 @@ def test_async_kernel_vs_oracle_and_row_stream(rd, weighted):
     """The row-stream SpMM with asynchronous gathers into a shared-memory ring (FP32 vectors):
     on a power-law graph with heavy rows (split into chunks by the pre-pass) and a ragged pair
     count, every column slab width agrees with the oracle at convergence, with the row-stream
-    kernel at fixed k, and with itself bitwise on a repeat and under a permutation."""
+    kernel at fixed k, and with itself bitwise on a repeat and under a permutation; new
+    weights are followed."""
+    kernel = "async"
     g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 37, 77, weights="lognormal" if weighted else None)
     assert np.diff(g.row_ptr).max() > 256  # heavy rows present
     G = rd.Graph.from_csr(g)
     ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=300, stop_tol=1e-14, threads=0)
+    code = 5
     for tile in [16, 32, 64, 128]:
-        kw = dict(mode="fp32", kernel="async", rhs_tile=tile, compact=False)
+        kw = dict(mode="fp32", kernel=kernel, rhs_tile=tile, compact=False)
         res = G.query(s, t, k_max=300, rel_tol=0.0, resid_tol=1e-7, **kw)
         st = G.last_stats()
-        assert st["kernel"] == 5 and st["rhs_tile"] == tile
+        assert st["kernel"] == code and st["rhs_tile"] == tile
         assert np.all(res.status >= 0)
         assert rel(res.r, ref).max() < FP32_TOL, (tile, rel(res.r, ref).max())
         fa = G.query(s, t, k_max=25, fixed_k=True, **kw)
@@ -207,12 +210,126 @@ def test_async_kernel_vs_oracle_and_row_stream(rd, weighted):
         perm = np.random.default_rng(1).permutation(len(s))
         fp = G.query(s[perm], t[perm], k_max=25, fixed_k=True, **kw)
         assert np.array_equal(fp.r, fa.r[perm])
-    # graph replay and the compacting default path with the async kernel
-    kw = dict(mode="fp32", kernel="async", rhs_tile=32, k_max=300, rel_tol=1e-7)
+    # graph replay and the compacting default path with this kernel
+    kw = dict(mode="fp32", kernel=kernel, rhs_tile=32, k_max=300, rel_tol=1e-7)
     a = G.query(s, t, **kw)
     b = G.query(s, t, graph=False, **kw)
     assert np.array_equal(a.r, b.r)
     assert rel(a.r, ref).max() < FP32_TOL
+    # new weights: the next query follows them
+    w2 = F.lognormal_edge_weights(g.m, 0.0, 0.7, 91)
+    g2 = F.weighted(g, w2)
+    G.set_weights(g2.w)
+    ref2, _, _ = lanczos.lanczos_batch(g2, s, t, k_max=300, stop_tol=1e-14, threads=0)
+    r2 = G.query(s, t, mode="fp32", kernel=kernel, rhs_tile=64, compact=False, k_max=300, rel_tol=0.0,
+                 resid_tol=1e-7).r
+    assert rel(r2, ref2).max() < FP32_TOL
+
+
+def _weakly_coupled(kind: str, eps: float):
+    """Cliques joined through one edge of weight eps: the Krylov space of a pair across the
+    weak edge is nearly invariant at some step, where beta_{i+1} / (|alpha_i| + beta_i)
+    falls to 1e-5 .. 1e-8 before the recurrence goes on."""
+    parts = [F.complete(40), F.path(10), F.complete(40)] if kind == "K40-P10-K40" else [F.complete(50), F.path(8)]
+    links = [(0, 0, 1, 0, eps), (1, 9, 2, 0, 1.0)] if kind == "K40-P10-K40" else [(0, 0, 1, 0, eps)]
+    off, A, B, Wt, offs = 0, [], [], [], []
+    for g in parts:
+        a, b, _ = g.undirected_edges()
+        A.append(a + off)
+        B.append(b + off)
+        Wt.append(np.ones(a.size))
+        offs.append(off)
+        off += g.n
+    for i, u, j, v, w in links:
+        A.append(np.array([offs[i] + u]))
+        B.append(np.array([offs[j] + v]))
+        Wt.append(np.array([w]))
+    g = to_csr(off, np.concatenate(A), np.concatenate(B), np.concatenate(Wt).astype(np.float32))
+    pairs = [(1, 55), (3, 45)] if kind == "K40-P10-K40" else [(1, 57), (4, 52)]
+    return g, np.array([p[0] for p in pairs], np.int32), np.array([p[1] for p in pairs], np.int32)
+
+
+@pytest.mark.parametrize("kind,eps", [("K40-P10-K40", 1e-2), ("K40-P10-K40", 1e-3), ("K50+P8", 1e-2),
+                                      ("K50+P8", 1e-3)])
+def test_near_invariant_krylov_steps(rd, kind, eps):
+    """Steps where beta_{i+1} is tiny against alpha_i (the cancellation regime of
+    beta_{i+1}^2 = ||w||^2 - alpha_i^2 - gamma^2): the FP64 and double-float paths follow the
+    oracle's r_k history at fixed k and converge to the dense pseudo-inverse value. The
+    tolerance is 1e-8, above the FP64 oracle's own error on these graphs (up to 2.5e-9 against
+    the dense reference: the weak edge makes them ill-conditioned)."""
+    g, s, t = _weakly_coupled(kind, eps)
+    ref = dense.DenseRD.of(g).r(s, t)
+    # the regime is reached: beta_{i+1} / (|alpha_i| + beta_i) below 1e-4 at some step
+    o = lanczos.lanczos_pair(g, int(s[0]), int(t[0]), k_max=60, stop_tol=1e-15)
+    k = o["k"]
+    ratio = o["beta"][1:k] / np.maximum(np.abs(o["alpha"][:k - 1]) + o["beta"][:k - 1], 1e-300)
+    assert ratio.min() < 1e-4, ratio.min()
+    G = rd.Graph.from_csr(g)
+    for mode in ("fp64", "df64"):
+        for onchip in (False, True):
+            if mode == "df64" and onchip:
+                continue  # double-float vectors: multi-kernel path only
+            # the weak edge slows convergence: up to about 500 steps to residual 1e-11
+            res = G.query(s, t, mode=mode, k_max=3000, rel_tol=0.0, resid_tol=1e-11, onchip=onchip)
+            if mode == "fp64":
+                assert np.all(res.status == 0), (mode, onchip, res.status, res.iters)
+            else:
+                # double-float vectors (about 48 bits) can lose definiteness of I - T_k after such
+                # a step: the pair then stops flagged RD_ERR_NUMERIC, never silently
+                assert np.all((res.status == 0) | (res.status == rd.RD_ERR_NUMERIC)), res.status
+                assert np.any(res.status == 0)
+            ok = res.status == 0
+            assert rel(res.r[ok], ref[ok]).max() < 1e-8, (mode, onchip, rel(res.r, ref).max())
+    for kk in (4, 8, 12, 14):
+        orc = np.array([lanczos.lanczos_pair(g, int(a), int(b), k_max=kk)["r"] for a, b in zip(s, t)])
+        res = G.query(s, t, mode="fp64", k_max=kk, fixed_k=True, onchip=False)
+        m = res.iters == kk
+        assert m.any()
+        assert rel(res.r[m], orc[m]).max() < 1e-8, (kk, rel(res.r[m], orc[m]).max())
+
+
+@pytest.mark.parametrize("mode,tol,hist_tol", [("fp64", FP64_TOL, 1e-11), ("fp32", FP32_TOL, 2e-5)])
+def test_cluster_whole_recurrence_vs_oracle(rd, mode, tol, hist_tol):
+    """Small graphs and few pairs: each pair's whole recurrence runs on a thread-block cluster
+    (CTAs holding slices of the vectors, reading each other's through distributed shared
+    memory). Against the dense pseudo-inverse or the grid closed form at convergence, the
+    oracle's r_k at fixed k, and the one-CTA kernel; a vertex count that no cluster size
+    divides, weights, and a heavy row (star centre) included."""
+    star = F.star(900)
+    cases = [("grid64", W.grid64()[0], np.array([0], np.int32), np.array([4095], np.int32)),
+             ("rc1000ln", F.random_connected(1000, 3000, 5, "lognormal"), None, None),
+             ("grid37del", F.grid_deleted(37, 0.05, 2), None, None),
+             ("star900", star, np.array([3, 10, 0], np.int32), np.array([500, 899, 7], np.int32))]
+    for name, g, s, t in cases:
+        if s is None:
+            s, t = F.random_pairs(g.n, 3, 11)
+        ref = (np.array([CF.grid_r(64, 64, 0, 4095)]) if name == "grid64" else dense.DenseRD.of(g).r(s, t))
+        G = rd.Graph.from_csr(g)
+        kw = dict(mode=mode, k_max=600, rel_tol=0.0, resid_tol=1e-11 if mode == "fp64" else 1e-6)
+        res = G.query(s, t, **kw)
+        ctas = G.last_stats()["onchip_ctas"]
+        assert ctas > 1, (name, ctas)
+        assert np.all(res.status == 0), (name, res.status)
+        assert rel(res.r, ref).max() < tol, (name, ctas, rel(res.r, ref).max())
+        one = G.query(s, t, cluster=False, **kw)
+        assert G.last_stats()["onchip_ctas"] == 1
+        assert rel(res.r, one.r).max() < tol, name
+        k = 12
+        orc = [lanczos.lanczos_pair(g, int(a), int(b), k_max=k) for a, b in zip(s, t)]
+        fk = G.query(s, t, mode=mode, k_max=k, fixed_k=True)
+        assert G.last_stats()["onchip_ctas"] > 1
+        # pairs that run all k steps match the oracle's r_k; pairs that break down earlier (the
+        # star's Krylov spaces are tiny) hold the exact value, T_i being exact at breakdown
+        ko = np.array([o["k"] for o in orc])
+        ro = np.array([o["r"] for o in orc])
+        m = (fk.iters == k) & (ko == k)
+        if m.any():
+            assert rel(fk.r[m], ro[m]).max() < hist_tol, (name, rel(fk.r[m], ro[m]).max())
+        b = fk.iters < k
+        if b.any():
+            assert rel(fk.r[b], ref[b]).max() < tol, (name, fk.iters, rel(fk.r[b], ref[b]).max())
+        assert m.any() or b.all(), (name, fk.iters, ko)
+        assert np.array_equal(G.query(s, t, mode=mode, k_max=k, fixed_k=True).r, fk.r)  # deterministic
 
 
 def test_scaling_by_four_is_bitwise(rd):
