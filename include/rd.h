@@ -120,6 +120,12 @@ typedef enum {
                                (one per SM), each holding a slice of the three vectors in its shared
                                memory and reading the others' through distributed shared memory; the
                                two agree to rounding */
+#define RD_Q_NO_DEVICE_LOOP 4096u /* rd_query: launch each step's CUDA graph from the host and poll
+                               the active count between steps. By default the steps after the first
+                               run in one graph whose conditional (while) node repeats the step on
+                               the device until every pair has stopped, k_max is reached or a column
+                               compaction is due; the host steps in only to pack the columns. Both
+                               give bitwise the same results */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */
@@ -171,6 +177,8 @@ typedef struct {
                                 (see RD_Q_DENSE_FIRST) */
     int32_t onchip_ctas;     /* CTAs per pair of the whole-recurrence kernel (1: one CTA, 2..16: a
                                 thread-block cluster; see RD_Q_NO_CLUSTER), 0 if it did not run */
+    int32_t device_loop;     /* 1 if the steps after the first ran in the device-resident loop
+                                (see RD_Q_NO_DEVICE_LOOP) */
 } rd_call_stats;
 
 /* Fill `opts` with defaults: k_max 1000, rel_tol 1e-7, resid_tol 0, FP32 vectors with FP64

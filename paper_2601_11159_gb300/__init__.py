@@ -26,6 +26,7 @@ from ._lib import (  # noqa: F401
     RD_MODE_FP64, RD_MODE_FP32V_FP64S, RD_MODE_DF64, RD_INPUT_ON_DEVICE, RD_CHECK_SYMMETRY, RD_LABEL_COMPONENTS,
     RD_Q_FIXED_K, RD_Q_NO_DEFLATE, RD_Q_PLAIN, RD_Q_PROFILE, RD_Q_NO_COMPACT, RD_Q_NO_ONCHIP, RD_Q_NO_TUNE,
     RD_Q_NO_GRAPH, RD_Q_EST_DELAYED, RD_Q_DENSE_FIRST, RD_Q_REPLAY_POTENTIAL, RD_Q_NO_CLUSTER,
+    RD_Q_NO_DEVICE_LOOP,
 )
 
 __all__ = ["Graph", "RDError", "query", "edge_grad", "potential", "graph_create", "graph_destroy",
@@ -104,7 +105,7 @@ def _check(st: int, where: str, ok=(RD_OK, RD_WARN_NOT_CONVERGED)):
 def _opts(k_max=1000, rel_tol=1e-7, resid_tol=0.0, mode="fp32", rhs_tile=0, rows_per_warp=0, chunk_steps=0,
           fixed_k=False, deflate=True, plain=False, profile=False, kernel=0, compact=True,
           onchip=True, tune=True, graph=True, estimate="geometric", sparse_first=True,
-          potential_mode="direct", cluster=True) -> _lib.QueryOpts:
+          potential_mode="direct", cluster=True, device_loop=True) -> _lib.QueryOpts:
     o = _lib.QueryOpts()
     lib().rd_query_opts_init(C.byref(o))
     o.k_max = int(k_max)
@@ -128,7 +129,8 @@ def _opts(k_max=1000, rel_tol=1e-7, resid_tol=0.0, mode="fp32", rhs_tile=0, rows
                (0 if compact else RD_Q_NO_COMPACT) | (0 if onchip else RD_Q_NO_ONCHIP) |
                (0 if tune else RD_Q_NO_TUNE) | (0 if graph else RD_Q_NO_GRAPH) |
                (RD_Q_EST_DELAYED if estimate == "delayed" else 0) | (0 if sparse_first else RD_Q_DENSE_FIRST) |
-               (RD_Q_REPLAY_POTENTIAL if potential_mode == "replay" else 0) | (0 if cluster else RD_Q_NO_CLUSTER))
+               (RD_Q_REPLAY_POTENTIAL if potential_mode == "replay" else 0) | (0 if cluster else RD_Q_NO_CLUSTER) |
+               (0 if device_loop else RD_Q_NO_DEVICE_LOOP))
     if estimate not in ("geometric", "delayed"):
         raise ValueError(f"unknown estimate {estimate!r}")
     if potential_mode not in ("direct", "replay"):

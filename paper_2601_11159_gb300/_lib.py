@@ -44,6 +44,7 @@ RD_Q_EST_DELAYED = 256
 RD_Q_DENSE_FIRST = 512
 RD_Q_REPLAY_POTENTIAL = 1024
 RD_Q_NO_CLUSTER = 2048
+RD_Q_NO_DEVICE_LOOP = 4096
 
 
 class QueryOpts(C.Structure):
@@ -77,6 +78,7 @@ class CallStats(C.Structure):
         ("row_order", C.c_int32),
         ("sparse_first", C.c_int32),
         ("onchip_ctas", C.c_int32),
+        ("device_loop", C.c_int32),
     ]
 
 

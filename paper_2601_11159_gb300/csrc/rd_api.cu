@@ -498,6 +498,8 @@ struct Buffers {
     int32_t* summary;
     int32_t* err_flag;
     int32_t* step_dev;        // step index of graph-replayed steps (zeroed per query)
+    int32_t* loop_saved;      // [3]: steps done j when the device-resident loop stopped, active after j-1, j
+    int32_t* loop_cfrom;      // first step at which the loop tests for a column compaction
     // gradient / potential
     void* phi;
     void* pvec;               // n x ld0: direction vectors of the potential's direct update
@@ -555,6 +557,8 @@ static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, boo
     b->summary = c.take<int32_t>(2);
     b->err_flag = c.take<int32_t>(1);
     b->step_dev = c.take<int32_t>(1);
+    b->loop_saved = c.take<int32_t>(4);
+    b->loop_cfrom = c.take<int32_t>(1);
     b->xcf = grad ? c.take<char>(K * 2 * ld * pl.elem) : nullptr;
     c.off = (c.off + 255) & ~size_t(255);
     b->state_bytes_end = c.off;
@@ -618,6 +622,7 @@ struct RunCtx {
     bool onchip = false;     // whole recurrence per pair in one kernel (small graphs, queries only)
     int onchip_ctas = 0;     // CTAs per pair it ran with (1, or a cluster of 2..16)
     bool graph = false;      // steps replayed from a captured CUDA graph of one step
+    bool device_loop = false;  // steps after the first run by the device-resident loop
     bool sparse_first = false;  // first step run by k_step0_sparse
     bool pot_x = false;      // potential accumulated during the forward steps (k_normalize_pot)
     int compactions = 0;
@@ -973,6 +978,95 @@ static rd_status launch_step_graph(RunCtx& c, const FinArgs& base)
     return RD_OK;
 }
 
+// The device-resident step loop: one CUDA graph whose conditional while node repeats a body of
+// k_loop_cond and one Lanczos step for each orientation of the two vector blocks (condition,
+// step, condition, step), so that the steps of a query run without the host until every pair
+// has stopped, k_max is reached or a column compaction is due. The steps it ran are read back
+// by the caller (loop_saved).
+template <typename T>
+static rd_status launch_step_loop(RunCtx& c, const FinArgs& base, int compact_check, int lag)
+{
+    rd_graph* g = c.g;
+    StepArgs<T> sa[2];
+    FinArgs fa[2];
+    NormArgs<T> na[2];
+    graph_step_args<T>(c, base, &sa[0], &fa[0], &na[0]);
+    std::swap(c.b.q[0], c.b.q[1]);
+    graph_step_args<T>(c, base, &sa[1], &fa[1], &na[1]);
+    std::swap(c.b.q[0], c.b.q[1]);
+    const bool heavy = g->n_chunks > 0;
+    int misc[10] = {c.cur.cfg.vec, c.cur.cfg.gs, c.cur.cfg.nzl, c.cur.cfg.kind, c.cur.grid_main, c.cur.grid_heavy,
+                    c.cur.grid_norm, c.pl.k_max, compact_check, lag};
+    std::string key("loop");
+    key.append(reinterpret_cast<const char*>(misc), sizeof(misc));
+    for (int o = 0; o < 2; ++o) {
+        key.append(reinterpret_cast<const char*>(&sa[o]), sizeof(sa[o]));
+        key.append(reinterpret_cast<const char*>(&fa[o]), sizeof(fa[o]));
+        key.append(reinterpret_cast<const char*>(&na[o]), sizeof(na[o]));
+    }
+    key.push_back(std::is_same<T, df64>::value ? 'w' : (sizeof(T) == 8 ? 'd' : 'f'));
+    cudaGraphExec_t exec = nullptr;
+    for (const auto& kv : g->graphs)
+        if (kv.first == key) {
+            exec = kv.second;
+            break;
+        }
+    if (!exec) {
+        if (!g->capture_stream) RD_CUDA(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = g->capture_stream;
+        cudaGraph_t graph = nullptr;
+        RD_CUDA(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle h;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_status(e, "building the device-resident step loop");
+        }
+        bool ok = true;
+        for (int o = 0; o < 2 && ok; ++o) {
+            launch_loop_cond(cs, h, c.b.step_dev, c.b.st.act_count, c.b.loop_saved, c.b.loop_cfrom, c.pl.k_max,
+                             c.cur.ld, compact_check, lag);
+            if (heavy) ok = launch_spmm_t(c.cur.cfg, g->weighted, true, c.cur.grid_heavy, cs, sa[o]);
+            if (ok) ok = launch_spmm_t(c.cur.cfg, g->weighted, false, c.cur.grid_main, cs, sa[o]);
+            if (ok) {
+                launch_finalize(cs, fa[o]);
+                launch_normalize_t(c.cur.grid_norm, cs, na[o]);
+                launch_step_advance(cs, c.b.step_dev, c.pl.k_max);
+            }
+        }
+        cudaGraph_t body = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &body);
+        if (!ok || ec != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            if (!ok) {
+                set_error("no SpMM kernel for this configuration");
+                return RD_ERR_UNSUPPORTED;
+            }
+            return cuda_status(ec, "cudaStreamEndCapture (step loop)");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        RD_CUDA(ei);
+        if (g->graphs.size() >= kGraphCache) {
+            cudaGraphExecDestroy(g->graphs.front().second);
+            g->graphs.erase(g->graphs.begin());
+        }
+        g->graphs.emplace_back(std::move(key), exec);
+    }
+    RD_CUDA(cudaGraphLaunch(exec, c.st));
+    return RD_OK;
+}
+
 // Algorithmic bytes of one SpMM launch above which rd_query polls without lag (about a
 // quarter of a millisecond of HBM traffic on this part, against a host reaction of tens of
 // microseconds).
@@ -1048,7 +1142,44 @@ static rd_status run_forward(RunCtx& c)
     int last_known = h[1];
     const bool sparse0 = sparse_first_step(c);
     c.sparse_first = sparse0;
+    // rd_query: after the first step, a device-resident loop over the steps (the host steps in
+    // only for column compactions)
+    const bool dloop = c.graph && c.lagged_polls && (c.o.flags & RD_Q_NO_DEVICE_LOOP) == 0;
+    c.device_loop = dloop;
     for (int j = 0; j < c.pl.k_max; ++j) {
+        if (dloop && j > 0) {
+            const int compact_check = c.compact ? 1 : 0;
+            const int per_step = (c.g->n_chunks > 0 ? 2 : 1) + 4;
+            while (true) {
+                const int j0 = c.steps;
+                const double bytes_per_step = spmm_launch_bytes(c.g, c.cur);
+                const int lag = bytes_per_step > kNoLagBytes ? 0 : 1;  // as the host polls below
+                RD_TRY(launch_step_loop<T>(c, fa, compact_check, lag));
+                // the step index back from the sentinel, for the next launch
+                RD_CUDA(cudaMemcpyAsync(c.b.step_dev, c.b.loop_saved, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                        c.st));
+                RD_CUDA(cudaMemcpyAsync(h + 8, c.b.loop_saved, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+                RD_CUDA(cudaStreamSynchronize(c.st));
+                const int jn = h[8];
+                const int ran = jn - j0;
+                // body passes: the stop shows at the first condition of pass ran/2 + 1 (even ran)
+                // or at the middle one of pass (ran + 1)/2 (odd); every kernel of a pass launches
+                c.launches += (int64_t)(ran / 2 + 1) * 2 * per_step;
+                c.spmm_launches += ran;
+                c.spmm_bytes += bytes_per_step * ran;
+                if (ran & 1) std::swap(c.b.q[0], c.b.q[1]);
+                c.steps = jn;
+                const int act = h[10], act_lag = lag ? h[9] : h[10];  // counts after jn and jn - 1 steps
+                if (act == 0 || jn >= c.pl.k_max) break;
+                const int64_t ld_before = c.cur.ld;
+                RD_TRY(enqueue_compaction<T>(c, act_lag));
+                if (c.cur.ld == ld_before) {  // no narrower layout now: test again after one more step
+                    h[11] = jn + 1;
+                    RD_CUDA(cudaMemcpyAsync(c.b.loop_cfrom, h + 11, sizeof(int32_t), cudaMemcpyHostToDevice, c.st));
+                }
+            }
+            break;
+        }
         const bool sparse = j == 0 && sparse0;
         if (c.graph && !sparse) {
             RD_TRY(launch_step_graph<T>(c, fa));
@@ -1079,6 +1210,7 @@ static rd_status run_forward(RunCtx& c)
         std::swap(c.b.q[0], c.b.q[1]);
         c.steps = j + 1;
         if (j + 1 >= c.pl.k_max) break;
+        if (dloop) continue;  // the device-resident loop reads the active counts itself
         if (c.lagged_polls) {
             // count of active pairs after step j lands in h[4 + j % kSlots]; read the count
             // of the previous step, whose copy has usually completed while step j runs --
@@ -1158,6 +1290,7 @@ static void record_stats(RunCtx& c)
     s.row_order = c.pl.cfg.order;
     s.sparse_first = c.sparse_first ? 1 : 0;
     s.onchip_ctas = c.onchip_ctas;
+    s.device_loop = c.device_loop ? 1 : 0;
     if (c.profile) {
         double ms = 0.0;
         for (auto& pr : c.spmm_ev) {

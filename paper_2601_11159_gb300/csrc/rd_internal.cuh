@@ -322,6 +322,12 @@ void launch_split_df(cudaStream_t st, int grid, int64_t n, const double* src, df
 void launch_finalize(cudaStream_t st, const FinArgs& a);
 // Advance the device step index by one, saturating at `limit` (end of a replayed step).
 void launch_step_advance(cudaStream_t st, int32_t* step, int limit);
+// Condition kernel of the device-resident step loop (a conditional while node): with *step
+// steps done, continue while pairs are active, k_max is not reached and no column compaction
+// is due; on stop, record the steps done and the active counts after j - 1 and j steps in
+// saved[0..2] and park *step at k_max + 1.
+void launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, int32_t* step, const int32_t* act_count,
+                      int32_t* saved, const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag);
 
 struct InitArgs {
     int64_t n, ld;

@@ -382,22 +382,45 @@ __device__ __forceinline__ void row_epilogue(const StepArgs<T>& a, int64_t row, 
     }
 }
 
-// Sum of the heavy row's chunk partials (chunk order, NZL lanes strided).
-template <typename T, int VEC, int NZL>
-__device__ __forceinline__ void heavy_row_sum(const StepArgs<T>& a, int64_t row, int64_t c0, int zl, T (&acc)[VEC])
+// Index of a heavy row in the sorted heavy_rows list (binary search).
+template <typename T>
+__device__ __forceinline__ int heavy_index(const StepArgs<T>& a, int64_t row)
 {
     int64_t lo = 0, hi = a.n_heavy_rows - 1;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         if (a.heavy_rows[mid] < row) lo = mid + 1; else hi = mid;
     }
-    const int f = a.heavy_first[lo], l = a.heavy_first[lo + 1];
-    for (int c = f + zl; c < l; c += NZL) {
-        T x[VEC];
-        ld_plain<T, VEC>(x, a.heavy_part + (int64_t)c * a.ld + c0);
+    return (int)lo;
+}
+
+// Sum of the chunk partials [f, l) of a heavy row (chunk order, NZL lanes strided; up to four
+// partials loaded before they are added, in the same order, as registers allow).
+template <typename T, int VEC, int NZL>
+__device__ __forceinline__ void heavy_chunks_sum(const StepArgs<T>& a, int f, int l, int64_t c0, int zl,
+                                                 T (&acc)[VEC])
+{
+    constexpr int U = sizeof(T) * VEC <= 8 ? 4 : (sizeof(T) * VEC <= 16 ? 2 : 1);
+    for (int c = f + zl; c < l; c += U * NZL) {
+        T x[U][VEC];
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) acc[i] += x[i];
+        for (int u = 0; u < U; ++u)
+            if (c + u * NZL < l) ld_plain<T, VEC>(x[u], a.heavy_part + (int64_t)(c + u * NZL) * a.ld + c0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (c + u * NZL < l) {
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) acc[i] += x[u][i];
+            }
     }
+}
+
+// Sum of the heavy row's chunk partials (chunk order, NZL lanes strided).
+template <typename T, int VEC, int NZL>
+__device__ __forceinline__ void heavy_row_sum(const StepArgs<T>& a, int64_t row, int64_t c0, int zl, T (&acc)[VEC])
+{
+    const int hi = heavy_index(a, row);
+    heavy_chunks_sum<T, VEC, NZL>(a, a.heavy_first[hi], a.heavy_first[hi + 1], c0, zl, acc);
 }
 
 // Partial sums of each heavy-row chunk: heavy_part[chunk, :] = sum over the chunk's nonzeros.
@@ -891,9 +914,18 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, VEC>) k_spmm_rows(const 
 #ifndef RD_ASYNC_MINB
 #define RD_ASYNC_MINB 2
 #endif
+// rows ahead whose own-row operands q_{i-1}[row] and q_i[row] are prefetched into L2 (0: none)
+#ifndef RD_ASYNC_PF_DIST
+#define RD_ASYNC_PF_DIST 1
+#endif
 constexpr int kAsyncDepth = RD_ASYNC_DEPTH;  // gathers in flight per lane
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
 {
@@ -957,8 +989,27 @@ struct AsyncRound {
     }
 };
 
-// Stream the nonzeros [eb, ee) of one row group through the ring: `enter(e)` runs before
-// nonzero e is added (row epilogues at row boundaries), then acc += w_e * q[col_e, slab].
+// acc += w * x (or acc += x unweighted) on the four columns of a lane
+template <bool WEIGHTED>
+__device__ __forceinline__ void acc_add4(float (&acc)[4], const float4& x, float wv)
+{
+    if constexpr (WEIGHTED) {
+        acc[0] = fmaf(wv, x.x, acc[0]);
+        acc[1] = fmaf(wv, x.y, acc[1]);
+        acc[2] = fmaf(wv, x.z, acc[2]);
+        acc[3] = fmaf(wv, x.w, acc[3]);
+    } else {
+        acc[0] += x.x;
+        acc[1] += x.y;
+        acc[2] += x.z;
+        acc[3] += x.w;
+    }
+}
+
+// Stream the nonzeros [eb, ee) of one row group through the ring: acc += w_e * q[col_e, slab].
+// `enter(e)` runs before nonzero e is added when e may open a new row (it closes the rows
+// that end there: row epilogues) and returns the end of the segment that e is in (the first
+// nonzero of the next row); each segment is then consumed without a boundary test per nonzero.
 template <int GS, bool WEIGHTED, class Enter>
 __device__ __forceinline__ void async_stream(const StepArgs<float>& a, const float* q, uint32_t ldv, int eb, int ee,
                                              uint32_t ring, int gl, unsigned mask, float (&acc)[4], Enter&& enter)
@@ -977,27 +1028,21 @@ __device__ __forceinline__ void async_stream(const StepArgs<float>& a, const flo
     for (int base = eb; base < ee; base += D) {
         nn.load(a, base + 2 * D, ee, gl, ldv);
         const int cnt = ee - base < D ? ee - base : D;
-        for (int u = 0; u < cnt; ++u) {
-            const int e = base + u;
+        const int refill = ee - D - base;  // slots u < refill are refilled from the next round
+        auto consume = [&](int u) {
             float wv = 1.0f;
             if constexpr (WEIGHTED) wv = __shfl_sync(mask, cur.w_at(u), u % GS, GS);
             const uint32_t o = __shfl_sync(mask, nxt.off_at(u), u % GS, GS);
             cp_async_wait<D - 1>();
             const float4 x = lds_f4(ring + u * SS);
-            enter(e);
-            if constexpr (WEIGHTED) {
-                acc[0] = fmaf(wv, x.x, acc[0]);
-                acc[1] = fmaf(wv, x.y, acc[1]);
-                acc[2] = fmaf(wv, x.z, acc[2]);
-                acc[3] = fmaf(wv, x.w, acc[3]);
-            } else {
-                acc[0] += x.x;
-                acc[1] += x.y;
-                acc[2] += x.z;
-                acc[3] += x.w;
-            }
-            if (e + D < ee) cp_async16(ring + u * SS, q + (size_t)o * 4);
+            acc_add4<WEIGHTED>(acc, x, wv);
+            if (u < refill) cp_async16(ring + u * SS, q + (size_t)o * 4);
             cp_async_commit();
+        };
+        for (int u = 0; u < cnt;) {
+            const int se = enter(base + u) - base;
+            const int stop = se < cnt ? se : cnt;
+            for (; u < stop; ++u) consume(u);
         }
         cur = nxt;
         nxt = nn;
@@ -1026,19 +1071,21 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async_heavy(cons
         for (int64_t ch = gid; ch < a.n_chunks; ch += ngroups) {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             async_stream<GS, WEIGHTED>(a, q, ldv, a.chunk_beg[ch], a.chunk_end[ch], ring, gl, mask, acc,
-                                       [](int) {});
+                                       [](int) { return INT_MAX; });
             st_plain<float, 4>(a.heavy_part + ch * a.ld + c0, acc);
         }
     }
 }
 
 // Main kernel: W = D^{-1} W_adj q_i - beta_i q_{i-1} over q_{i-1}, and the block partials of
-// sum d W q_i, sum d W^2, sum d W per column (slab by slab).
+// sum d W q_i, sum d W^2, sum d W per column (slab by slab). Row groups take the tasks
+// grid-strided; a task of light rows is one stream of nonzeros through the ring.
 template <int GS, bool WEIGHTED>
 __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const StepArgs<float> a)
 {
     constexpr int TP = 4 * GS;
     constexpr int NG = 32 / GS;
+    constexpr int PD = RD_ASYNC_PF_DIST;
     extern __shared__ __align__(16) float smem_f[];
     double(&red)[kWarps][TP] = *reinterpret_cast<double(*)[kWarps][TP]>(smem_f + kWarps * kAsyncDepth * 32 * 4);
     if (step_inactive(a)) return;
@@ -1059,17 +1106,18 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const Step
         ld_plain<float, 4>(bt, step_cf_beta(a) + c0);
         Acc<float> sA[4], sB[4], sC[4];
         const float* q = a.qcur + c0;
-        for (int task = gid; task < ntasks; task += ngroups) {
-            const int r0 = a.task_row[task], r1 = a.task_row[task + 1];
+        // a heavy row: the sum of its chunk partials [f, l)
+        auto heavy_row = [&](int r, int f, int l) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f}, qp[4], qc[4];
+            ld_stream<float, 4>(qp, a.qprev_w + (int64_t)r * ld + c0);
+            ld_gather<float, 4>(qc, q + (int64_t)r * ld);
+            heavy_chunks_sum<float, 4, 1>(a, f, l, c0, 0, acc);
+            row_epilogue<float, 4>(a, r, c0, a.invdeg[r], a.deg[r], acc, bt, qp, qc, sA, sB, sC);
+        };
+        // light rows [r0, r1): one stream of their nonzeros
+        auto light_rows = [&](int r0, int r1) {
             const int eb = (int)a.row_ptr[r0], ee = (int)a.row_ptr[r1];
             float acc[4] = {0.f, 0.f, 0.f, 0.f}, qp[4], qc[4];
-            if (r1 == r0 + 1 && ee - eb > a.heavy_thr) {
-                ld_stream<float, 4>(qp, a.qprev_w + (int64_t)r0 * ld + c0);
-                ld_gather<float, 4>(qc, q + (int64_t)r0 * ld);
-                heavy_row_sum<float, 4, 1>(a, r0, c0, 0, acc);
-                row_epilogue<float, 4>(a, r0, c0, a.invdeg[r0], a.deg[r0], acc, bt, qp, qc, sA, sB, sC);
-                continue;
-            }
             // row window: lane gl holds row_ptr[w0 + gl + 1], 1/d and d of row w0 + gl
             int w0 = r0;
             int my_end = (w0 + gl < r1) ? (int)a.row_ptr[w0 + gl + 1] : ee;
@@ -1079,6 +1127,14 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const Step
             int row_end = __shfl_sync(mask, my_end, 0, GS);
             ld_stream<float, 4>(qp, a.qprev_w + (int64_t)row * ld + c0);
             ld_gather<float, 4>(qc, q + (int64_t)row * ld);
+            // the own-row operands of the next PD rows into L2 (no registers held): short rows
+            // end before a load from DRAM would return
+#pragma unroll
+            for (int d = 1; d <= PD; ++d)
+                if (row + d < r1) {
+                    prefetch_l2(a.qprev_w + (int64_t)(row + d) * ld + c0);
+                    prefetch_l2(q + (int64_t)(row + d) * ld);
+                }
             // close the current row and open the next one
             auto next_row = [&]() {
                 const int wi = row - w0;
@@ -1098,11 +1154,25 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const Step
                 row_end = __shfl_sync(mask, my_end, row - w0, GS);
                 ld_stream<float, 4>(qp, a.qprev_w + (int64_t)row * ld + c0);
                 ld_gather<float, 4>(qc, q + (int64_t)row * ld);
+                if (PD > 0 && row + PD < r1) {
+                    prefetch_l2(a.qprev_w + (int64_t)(row + PD) * ld + c0);
+                    prefetch_l2(q + (int64_t)(row + PD) * ld);
+                }
             };
             async_stream<GS, WEIGHTED>(a, q, ldv, eb, ee, ring, gl, mask, acc, [&](int e) {
                 while (e >= row_end) next_row();
+                return row_end;
             });
-            while (row < r1) next_row();  // the last row (and rows without nonzeros after it)
+            while (row < r1) next_row();  // the last row (and any rows without nonzeros after it)
+        };
+        for (int task = gid; task < ntasks; task += ngroups) {
+            const int r0 = a.task_row[task], r1 = a.task_row[task + 1];
+            if (r1 == r0 + 1 && a.row_ptr[r1] - a.row_ptr[r0] > a.heavy_thr) {
+                const int hi = heavy_index(a, r0);
+                heavy_row(r0, a.heavy_first[hi], a.heavy_first[hi + 1]);
+                continue;
+            }
+            light_rows(r0, r1);
         }
         if (a.do_reduce) block_partials<float, 4, GS, TP>(a, sA, sB, sC, red, slab, lane, warp, gl);
     }

@@ -495,6 +495,43 @@ __global__ void k_step_advance(int32_t* step, int limit)
 
 void launch_step_advance(cudaStream_t st, int32_t* step, int limit) { k_step_advance<<<1, 1, 0, st>>>(step, limit); }
 
+// Condition of the device-resident step loop (a conditional while node of a CUDA graph): with
+// j steps done, go on while pairs are active, k_max is not reached and no column compaction is
+// due. The compaction test reads the count `lag` steps back (active pairs fit in half the
+// width), as rd_query's host polls do, so that both pack the columns at the same step. To stop,
+// record j and the active counts after j - 1 and j steps in saved[0..2] (one read for the
+// host) and move the step index to the sentinel k_max + 1, whose active count is always 0, so
+// that the remaining kernels of the loop body return at once; an index already at the
+// sentinel stays there.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, int32_t* step, const int32_t* act_count, int32_t* saved,
+                            const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag)
+{
+    const int j = *step;
+    if (j > k_max) {
+        cudaGraphSetConditional(h, 0);
+        return;
+    }
+    const int act = act_count[j];
+    // compaction is tested from step *compact_from on (the host moves it past a step where
+    // packing found no narrower layout)
+    const bool compact_due = compact_check && j >= lag + 1 && j >= *compact_from && ld > 16 &&
+                             (int64_t)act_count[j - lag] * 2 <= ld;
+    const bool go = act > 0 && j < k_max && !compact_due;
+    if (!go) {
+        saved[0] = j;
+        saved[1] = j > 0 ? act_count[j - 1] : act;
+        saved[2] = act;
+        *step = k_max + 1;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+void launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, int32_t* step, const int32_t* act_count,
+                      int32_t* saved, const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag)
+{
+    k_loop_cond<<<1, 1, 0, st>>>(h, step, act_count, saved, compact_from, k_max, ld, compact_check, lag);
+}
+
 // ------------------------------------------------------- sparse first step
 // q_1 is nonzero only in rows s and t of its column, so the first product
 // W = D^{-1} A q_1 (Algorithm 3 with q_0 = 0) is nonzero only on the rows adjacent to s or

@@ -419,7 +419,8 @@ def test_compaction_matches_fixed_layout(rd, mode):
         ref = dense.DenseRD.of(g).r(s, t)
         tol_ab, tol_ref = 1e-8, 1e-8
     else:
-        g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 200, 31)
+        # mean degree 4: the pairs need 10 to 16 steps, so half of them stop while the rest run on
+        g, s, t = W.chunglu(20000, 2.1, 4.0, 40000, 200, 31)
         kw = dict(mode=mode, k_max=200, rel_tol=1e-7)
         ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=200, stop_tol=1e-13, threads=0)
         tol_ab, tol_ref = 2e-6, FP32_TOL
@@ -428,10 +429,38 @@ def test_compaction_matches_fixed_layout(rd, mode):
     a = G.query(s, t, **kw)
     st = G.last_stats()
     b = G.query(s, t, compact=False, **kw)
-    assert st["compactions"] >= 1
+    assert st["compactions"] >= 1 and st["device_loop"] == 1
     assert np.abs(a.iters.astype(int) - b.iters.astype(int)).max() <= 1
     assert rel(a.r, b.r).max() < tol_ab
     assert rel(a.r, ref).max() < tol_ref
+    # the host-driven loop packs at the same steps: bitwise the same results
+    c = G.query(s, t, device_loop=False, **kw)
+    assert np.array_equal(c.r, a.r) and np.array_equal(c.iters, a.iters)
+    assert G.last_stats()["compactions"] >= st["compactions"]
+
+
+def test_async_kernel_scattered_heavy_rows(rd):
+    """The async kernel's row groups take contiguous shares of the tasks and stream each run of
+    light rows between heavy rows without a break; the pre-pass streams runs of contiguous
+    chunks. On R-MAT, whose heavy rows are scattered among light ones (not the leading ids as
+    in Chung-Lu), every tile width agrees with the oracle and with the row-stream kernel."""
+    from graphgen.graph import largest_component
+
+    g = largest_component(F.rmat(15, 16, 0.57, 0.19, 0.19, 12))
+    d = np.diff(g.row_ptr)
+    heavy = np.nonzero(d > 256)[0]
+    assert heavy.size > 10 and np.any(np.diff(heavy) > 1)  # heavy rows present, not contiguous
+    s, t = F.random_pairs(g.n, 53, 19)
+    G = rd.Graph.from_csr(g)
+    ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=300, stop_tol=1e-14, threads=0)
+    for tile in [16, 32, 64, 128]:
+        kw = dict(mode="fp32", kernel="async", rhs_tile=tile, compact=False)
+        res = G.query(s, t, k_max=300, rel_tol=0.0, resid_tol=1e-7, **kw)
+        assert G.last_stats()["kernel"] == 5
+        assert rel(res.r, ref).max() < FP32_TOL, (tile, rel(res.r, ref).max())
+        fa = G.query(s, t, k_max=20, fixed_k=True, **kw)
+        fs = G.query(s, t, mode="fp32", kernel="stream", rhs_tile=tile, compact=False, k_max=20, fixed_k=True)
+        assert rel(fa.r, fs.r).max() < 2e-6, (tile, rel(fa.r, fs.r).max())
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
@@ -622,21 +651,33 @@ def test_autotuner_first_use_and_arguments(rd):
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
 def test_graph_replay_is_bitwise_the_launch_loop(rd, mode):
-    """Steps replayed from the captured one-step CUDA graph (step index in device memory)
-    give bitwise the results of launching every kernel from the host: compacting query with
-    the error-estimate stop, fixed k, the plain path, and the gradient (potential built
+    """Steps replayed from the captured one-step CUDA graph (step index in device memory),
+    and the device-resident loop (a conditional while node repeating the step until every
+    pair stops or a column compaction is due), give bitwise the results of launching every
+    kernel from the host: compacting query with the error-estimate stop, fixed k, a k_max
+    reached with pairs still active, the plain path, and the gradient (potential built
     during the forward steps, or by the replay pass, which must regenerate the forward
     vectors)."""
     g, s, t = W.chunglu(20000, 2.1, 20.0, 200000, 70, 13)
     G = rd.Graph.from_csr(g)
-    for kw in (dict(k_max=200, rel_tol=1e-7), dict(k_max=200, rel_tol=0.0, resid_tol=1e-9),
-               dict(k_max=7, fixed_k=True), dict(k_max=200, rel_tol=1e-7, compact=False)):
+    for kw in (dict(k_max=5, rel_tol=1e-12), dict(k_max=200, rel_tol=1e-7),
+               dict(k_max=200, rel_tol=0.0, resid_tol=1e-9), dict(k_max=7, fixed_k=True),
+               dict(k_max=200, rel_tol=1e-7, compact=False)):
         a = G.query(s, t, mode=mode, **kw)
         ga = G.last_stats()
+        assert ga["device_loop"] == 1 and ga["steps"] <= kw["k_max"], kw
         b = G.query(s, t, mode=mode, graph=False, **kw)
+        gb = G.last_stats()
+        assert gb["device_loop"] == 0
         assert np.array_equal(a.r, b.r), kw
         assert np.array_equal(a.iters, b.iters) and np.array_equal(a.status, b.status), kw
-        assert ga["compactions"] == G.last_stats()["compactions"] or not kw.get("compact", True)
+        # the device loop tests the current count before packing, so it skips a packing after
+        # the last pair stopped that the lagged host poll still makes
+        assert ga["compactions"] <= gb["compactions"], kw
+        c = G.query(s, t, mode=mode, device_loop=False, **kw)  # one-step graph, host-driven
+        assert G.last_stats()["device_loop"] == 0
+        assert np.array_equal(c.r, b.r) and np.array_equal(c.iters, b.iters), kw
+        assert G.last_stats()["compactions"] == gb["compactions"], kw
     pa = G.query(s[:5], t[:5], mode=mode, plain=True, k_max=200, rel_tol=1e-7)
     pb = G.query(s[:5], t[:5], mode=mode, plain=True, k_max=200, rel_tol=1e-7, graph=False)
     assert np.array_equal(pa.r, pb.r) and np.array_equal(pa.iters, pb.iters)
@@ -710,7 +751,8 @@ def test_double_float_mode_batched_chunglu(rd):
     """Batched double-float query with the error-estimate stop, compaction and the tuned
     kernels on a power-law graph: within 1e-9 of the oracle; the other entry points run the
     mode as FP64."""
-    g, s, t = W.chunglu(30000, 2.1, 20.0, 300000, 100, 23)
+    # mean degree 4: the pairs need 21 to 27 steps, so most stop while the rest run on packed
+    g, s, t = W.chunglu(30000, 2.1, 4.0, 60000, 100, 23)
     G = rd.Graph.from_csr(g)
     ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=300, stop_tol=1e-15, threads=0)
     res = G.query(s, t, mode="df64", k_max=300, rel_tol=0.0, resid_tol=1e-11)
