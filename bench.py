@@ -281,10 +281,11 @@ def profile_config(rd, name, call="query"):
     elif call == "grad":
         ones = torch.ones(len(s), dtype=torch.float64, device="cuda")
         mode = "fp32"
-        kw = dict(mode=mode, k_max=200, rel_tol=1e-6)
+        kw = dict(mode=mode, k_max=200, rel_tol=1e-6, device_loop=False)
         run = lambda: G.edge_grad(sd, td, ones, **kw)  # noqa: E731
     else:
-        kw = dict(mode=mode, k_max=4, fixed_k=True)
+        # host-driven steps: ncu lists no kernels launched from a conditional graph node's body
+        kw = dict(mode=mode, k_max=4, fixed_k=True, device_loop=False)
         run = lambda: G.query(sd, td, **kw)  # noqa: E731
     run()
     torch.cuda.synchronize()
@@ -547,6 +548,9 @@ def main():
                     help="queries of the separate profiled pass that times the SpMM launches")
     ap.add_argument("--profile-pass-range", action="store_true",
                     help="bracket the first query of the profiled pass with cudaProfilerStart/Stop")
+    ap.add_argument("--no-device-loop", action="store_true",
+                    help="run the steps from the host-driven loop (for a per-kernel ncu launch list: ncu "
+                         "does not list kernels launched from a conditional graph node's body)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -588,6 +592,8 @@ def main():
     s_dev = torch.from_numpy(s_np).cuda()
     t_dev = torch.from_numpy(t_np).cuda()
     opts = dict(mode="fp32", k_max=K_MAX, rel_tol=REL_TOL, kernel=args.kernel, rhs_tile=args.rhs_tile)
+    if args.no_device_loop:  # the same kernels launched step by step (ncu lists them one by one)
+        opts["device_loop"] = False
     stream = torch.cuda.current_stream()
 
     # warm-up (also settles the workspace)

@@ -877,7 +877,7 @@ __global__ void __launch_bounds__(1024) k_compact_map(const CompactArgs a)
     }
 }
 
-// q blocks copied column-wise into the compact layout (empty slots zero).
+// q blocks copied column-wise into the compact layout (empty slots zero), any ld_new.
 template <typename T>
 __global__ void __launch_bounds__(256) k_compact_cols(const CompactArgs a)
 {
@@ -895,14 +895,53 @@ __global__ void __launch_bounds__(256) k_compact_cols(const CompactArgs a)
     }
 }
 
+// The same when ld_new is a multiple of the 16-byte unit V: thread t keeps one column unit
+// (its V source slots in registers) and walks the rows t / units, + rows_per_pass, ...;
+// each new row unit is one 16-byte store per block, and no index division runs per element.
+template <typename T>
+__global__ void __launch_bounds__(256) k_compact_cols_v(const CompactArgs a)
+{
+    constexpr int V = 16 / (int)sizeof(T);
+    const int64_t units = a.ld_new / V;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t rows_per_pass = (int64_t)gridDim.x * blockDim.x / units;
+    const int64_t r0 = t / units;
+    if (r0 >= rows_per_pass) return;  // threads past the last whole group of units
+    const int64_t cu = t % units;
+    int o[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) o[i] = a.old_slot[cu * V + i];
+    const T* s0 = static_cast<const T*>(a.q_src0);
+    const T* s1 = static_cast<const T*>(a.q_src1);
+    T* d0 = static_cast<T*>(a.q_dst0);
+    T* d1 = static_cast<T*>(a.q_dst1);
+    for (int64_t u = r0; u < a.n; u += rows_per_pass) {
+        T x0[V], x1[V];
+        const T* r0p = s0 + u * a.ld_old;
+        const T* r1p = s1 + u * a.ld_old;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            x0[i] = o[i] >= 0 ? r0p[o[i]] : T(0);
+            x1[i] = o[i] >= 0 ? r1p[o[i]] : T(0);
+        }
+        st_plain<T, V>(d0 + u * a.ld_new + cu * V, x0);
+        st_plain<T, V>(d1 + u * a.ld_new + cu * V, x1);
+    }
+}
+
 void launch_compact(cudaStream_t st, int grid, const CompactArgs& a)
 {
+    // the unit kernel needs whole 16-byte units per row and at least one row per pass
+    const int64_t v = 16 / a.elem_size;
+    const bool unit = a.ld_new % v == 0 && (int64_t)grid * 256 >= a.ld_new / v;
     if (a.elem_size == 8) {
         k_compact_map<double><<<1, 1024, 0, st>>>(a);
-        k_compact_cols<double><<<grid, 256, 0, st>>>(a);
+        if (unit) k_compact_cols_v<double><<<grid, 256, 0, st>>>(a);
+        else k_compact_cols<double><<<grid, 256, 0, st>>>(a);
     } else {
         k_compact_map<float><<<1, 1024, 0, st>>>(a);
-        k_compact_cols<float><<<grid, 256, 0, st>>>(a);
+        if (unit) k_compact_cols_v<float><<<grid, 256, 0, st>>>(a);
+        else k_compact_cols<float><<<grid, 256, 0, st>>>(a);
     }
 }
 
