@@ -498,7 +498,7 @@ struct Buffers {
     int32_t* summary;
     int32_t* err_flag;
     int32_t* step_dev;        // step index of graph-replayed steps (zeroed per query)
-    int32_t* loop_saved;      // [3]: steps done j when the device-resident loop stopped, active after j-1, j
+    int32_t* loop_saved;      // [4]: where the device-resident loop stopped (see launch_loop_cond)
     int32_t* loop_cfrom;      // first step at which the loop tests for a column compaction
     // gradient / potential
     void* phi;
@@ -706,6 +706,18 @@ static bool launch_spmm_t(const SpmmCfg& cfg, bool weighted, bool heavy, int gri
 static void launch_normalize_t(int grid, cudaStream_t st, const NormArgs<float>& a) { launch_normalize_f32(grid, st, a); }
 static void launch_normalize_t(int grid, cudaStream_t st, const NormArgs<double>& a) { launch_normalize_f64(grid, st, a); }
 static void launch_normalize_t(int grid, cudaStream_t st, const NormArgs<df64>& a) { launch_normalize_df64(grid, st, a); }
+static bool launch_normalize_pack_t(int grid, cudaStream_t st, const NormPackArgs<float>& a)
+{
+    return launch_normalize_pack_f32(grid, st, a);
+}
+static bool launch_normalize_pack_t(int grid, cudaStream_t st, const NormPackArgs<double>& a)
+{
+    return launch_normalize_pack_f64(grid, st, a);
+}
+static bool launch_normalize_pack_t(int grid, cudaStream_t st, const NormPackArgs<df64>& a)
+{
+    return launch_normalize_pack_df64(grid, st, a);
+}
 
 template <typename T>
 static rd_status enqueue_spmm(RunCtx& c, int j, bool reduce)
@@ -819,9 +831,14 @@ static void enqueue_init(RunCtx& c, bool replay)
 
 // Pack the columns of the still-active pairs into a block of ld_new columns (ld_new holds
 // at least `active_upper` slots, an upper bound on the active count read one step ago).
+// With fuse_step >= 0 the packing is fused with that step's normalise pass (its SpMM and
+// finalize have run: q[0] holds W and q[1] holds q_j): k_normalize_pack writes q_{j+1} and
+// q_j packed, and *fused reports whether it ran (the caller then runs the plain pass when it
+// did not: no narrower layout, or no whole 16-byte units).
 template <typename T>
-static rd_status enqueue_compaction(RunCtx& c, int active_upper)
+static rd_status enqueue_compaction(RunCtx& c, int active_upper, int fuse_step = -1, bool* fused = nullptr)
 {
+    if (fused) *fused = false;
     Plan np;
     rd_query_opts o2 = c.o;
     o2.rhs_tile = 0;
@@ -829,6 +846,7 @@ static rd_status enqueue_compaction(RunCtx& c, int active_upper)
     if (np.ld >= c.cur.ld) return RD_OK;
     // the spare region holds n x ld0 elements: two packed blocks must fit in it
     if (!c.in_region_x && 2 * np.ld > c.pl.ld) return RD_OK;
+    if (fuse_step >= 0 && np.ld % (16 / (int64_t)np.elem) != 0) return RD_OK;
     const int64_t n = c.g->n;
     void* dst0;
     void* dst1;
@@ -857,7 +875,26 @@ static rd_status enqueue_compaction(RunCtx& c, int active_upper)
     a.elem_size = (int)np.elem;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c.g->sm_count * 8,
                                                                  (n * np.ld + 255) / 256));
-    launch_compact(c.st, grid, a);
+    if (fuse_step >= 0) {
+        launch_compact_map(c.st, a);
+        NormPackArgs<T> na{};
+        na.n = n;
+        na.ld_old = c.cur.ld;
+        na.ld_new = np.ld;
+        na.w = static_cast<const T*>(c.b.q[0]);
+        na.qcur = static_cast<const T*>(c.b.q[1]);
+        na.cf = coef_block<T>(c, fuse_step);
+        na.old_slot = c.b.old_slot;
+        na.qnext_new = static_cast<T*>(dst1);  // q_{j+1}: the current block of the next step
+        na.qcur_new = static_cast<T*>(dst0);   // q_j: its previous block
+        if (!launch_normalize_pack_t(grid, c.st, na)) {
+            set_error("normalise-and-pack launch rejected");
+            return RD_ERR_UNSUPPORTED;
+        }
+        *fused = true;
+    } else {
+        launch_compact(c.st, grid, a);
+    }
     c.launches += 2;
     c.b.q[0] = dst0;
     c.b.q[1] = dst1;
@@ -979,10 +1016,11 @@ static rd_status launch_step_graph(RunCtx& c, const FinArgs& base)
 }
 
 // The device-resident step loop: one CUDA graph whose conditional while node repeats a body of
-// k_loop_cond and one Lanczos step for each orientation of the two vector blocks (condition,
-// step, condition, step), so that the steps of a query run without the host until every pair
-// has stopped, k_max is reached or a column compaction is due. The steps it ran are read back
-// by the caller (loop_saved).
+// one Lanczos step for each orientation of the two vector blocks, each step with a condition
+// before it and one after its finalize, so that the steps of a query run without the host
+// until every pair has stopped, k_max is reached or a column compaction is due (then after the
+// finalize of the step before it, so that the host runs that step's normalise pass fused with
+// the packing). Where it stopped is read back by the caller (loop_saved).
 template <typename T>
 static rd_status launch_step_loop(RunCtx& c, const FinArgs& base, int compact_check, int lag)
 {
@@ -1035,11 +1073,13 @@ static rd_status launch_step_loop(RunCtx& c, const FinArgs& base, int compact_ch
         bool ok = true;
         for (int o = 0; o < 2 && ok; ++o) {
             launch_loop_cond(cs, h, c.b.step_dev, c.b.st.act_count, c.b.loop_saved, c.b.loop_cfrom, c.pl.k_max,
-                             c.cur.ld, compact_check, lag);
+                             c.cur.ld, compact_check, lag, 0);
             if (heavy) ok = launch_spmm_t(c.cur.cfg, g->weighted, true, c.cur.grid_heavy, cs, sa[o]);
             if (ok) ok = launch_spmm_t(c.cur.cfg, g->weighted, false, c.cur.grid_main, cs, sa[o]);
             if (ok) {
                 launch_finalize(cs, fa[o]);
+                launch_loop_cond(cs, h, c.b.step_dev, c.b.st.act_count, c.b.loop_saved, c.b.loop_cfrom,
+                                 c.pl.k_max, c.cur.ld, compact_check, lag, 1);
                 launch_normalize_t(c.cur.grid_norm, cs, na[o]);
                 launch_step_advance(cs, c.b.step_dev, c.pl.k_max);
             }
@@ -1149,7 +1189,7 @@ static rd_status run_forward(RunCtx& c)
     for (int j = 0; j < c.pl.k_max; ++j) {
         if (dloop && j > 0) {
             const int compact_check = c.compact ? 1 : 0;
-            const int per_step = (c.g->n_chunks > 0 ? 2 : 1) + 4;
+            const int per_step = (c.g->n_chunks > 0 ? 2 : 1) + 5;
             while (true) {
                 const int j0 = c.steps;
                 const double bytes_per_step = spmm_launch_bytes(c.g, c.cur);
@@ -1158,25 +1198,37 @@ static rd_status run_forward(RunCtx& c)
                 // the step index back from the sentinel, for the next launch
                 RD_CUDA(cudaMemcpyAsync(c.b.step_dev, c.b.loop_saved, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                         c.st));
-                RD_CUDA(cudaMemcpyAsync(h + 8, c.b.loop_saved, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+                RD_CUDA(cudaMemcpyAsync(h + 8, c.b.loop_saved, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
                 RD_CUDA(cudaStreamSynchronize(c.st));
                 const int jn = h[8];
-                const int ran = jn - j0;
-                // body passes: the stop shows at the first condition of pass ran/2 + 1 (even ran)
-                // or at the middle one of pass (ran + 1)/2 (odd); every kernel of a pass launches
+                const int ran = jn - j0;  // steps run whole inside the loop
+                // body passes: the stop shows in pass ran/2 + 1, and every kernel of a pass launches
                 c.launches += (int64_t)(ran / 2 + 1) * 2 * per_step;
                 c.spmm_launches += ran;
                 c.spmm_bytes += bytes_per_step * ran;
                 if (ran & 1) std::swap(c.b.q[0], c.b.q[1]);
-                c.steps = jn;
-                const int act = h[10], act_lag = lag ? h[9] : h[10];  // counts after jn and jn - 1 steps
-                if (act == 0 || jn >= c.pl.k_max) break;
-                const int64_t ld_before = c.cur.ld;
-                RD_TRY(enqueue_compaction<T>(c, act_lag));
-                if (c.cur.ld == ld_before) {  // no narrower layout now: test again after one more step
-                    h[11] = jn + 1;
-                    RD_CUDA(cudaMemcpyAsync(c.b.loop_cfrom, h + 11, sizeof(int32_t), cudaMemcpyHostToDevice, c.st));
+                const int act_lag = h[9], act = h[10];  // the count the compaction test read; entering the next step
+                if (h[11]) {
+                    // stopped after step jn's finalize: its normalise pass, fused with the packing
+                    ++c.spmm_launches;
+                    c.spmm_bytes += bytes_per_step;
+                    bool fused = false;
+                    RD_TRY(enqueue_compaction<T>(c, act_lag, jn, &fused));
+                    if (!fused) {
+                        enqueue_normalize<T>(c, jn, false);
+                        std::swap(c.b.q[0], c.b.q[1]);
+                    }
+                    launch_step_advance(c.st, c.b.step_dev, c.pl.k_max);
+                    ++c.launches;
+                    c.steps = jn + 1;
+                } else {
+                    c.steps = jn;
+                    if (act == 0 || jn >= c.pl.k_max) break;
+                    RD_TRY(enqueue_compaction<T>(c, act_lag));
                 }
+                // the next test after one more step, as the host polls make it
+                h[12] = c.steps + 1;
+                RD_CUDA(cudaMemcpyAsync(c.b.loop_cfrom, h + 12, sizeof(int32_t), cudaMemcpyHostToDevice, c.st));
             }
             break;
         }

@@ -138,6 +138,18 @@ struct NormArgs {
     int64_t xcf_stride;
 };
 
+// Normalise pass fused with a column compaction (k_normalize_pack).
+template <typename T>
+struct NormPackArgs {
+    int64_t n, ld_old, ld_new;
+    const T* w;                    // W, old layout
+    const T* qcur;                 // q_i, old layout
+    const T* cf;                   // [4][ld_old]: beta_i, alpha_i, c_i, 1/beta_{i+1} of the step
+    const int32_t* old_slot;       // [ld_new]: source column of each packed column, -1 none
+    T* qnext_new;                  // q_{i+1}, packed (n x ld_new)
+    T* qcur_new;                   // q_i, packed (n x ld_new)
+};
+
 // Per-pair FP64 state of the running LDL^T factorisation of I - T_k.
 struct PairState {
     double* b2;        // ||b||^2 = 1/d_s + 1/d_t
@@ -222,6 +234,8 @@ struct CompactArgs {
     int elem_size;
 };
 void launch_compact(cudaStream_t st, int grid, const CompactArgs& a);
+// the slot maps and the packed coefficients only (the q blocks packed by the caller)
+void launch_compact_map(cudaStream_t st, const CompactArgs& a);
 
 // Power Method (Algorithm 1) in y = D^{-1} r: start y = D^{-1}(e_s - e_t), accumulate
 // rbar += (y_s - y_t)/2 per step (r(s)/(2 d_s) - r(t)/(2 d_t) of Algorithm 1).
@@ -318,16 +332,24 @@ std::vector<SpmmCfg> spmm_configs(bool fp64);
 void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a);
 void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a);
 void launch_normalize_df64(int grid, cudaStream_t st, const NormArgs<df64>& a);
+// false when the packed layout has no whole 16-byte units (the caller then packs separately)
+bool launch_normalize_pack_f32(int grid, cudaStream_t st, const NormPackArgs<float>& a);
+bool launch_normalize_pack_f64(int grid, cudaStream_t st, const NormPackArgs<double>& a);
+bool launch_normalize_pack_df64(int grid, cudaStream_t st, const NormPackArgs<df64>& a);
 void launch_split_df(cudaStream_t st, int grid, int64_t n, const double* src, df64* dst);
 void launch_finalize(cudaStream_t st, const FinArgs& a);
 // Advance the device step index by one, saturating at `limit` (end of a replayed step).
 void launch_step_advance(cudaStream_t st, int32_t* step, int limit);
-// Condition kernel of the device-resident step loop (a conditional while node): with *step
-// steps done, continue while pairs are active, k_max is not reached and no column compaction
-// is due; on stop, record the steps done and the active counts after j - 1 and j steps in
-// saved[0..2] and park *step at k_max + 1.
+// Condition kernels of the device-resident step loop (a conditional while node). Before step
+// j (*step = j): continue while pairs are active, k_max is not reached and no column
+// compaction is due. After step j's finalize (after_finalize = 1): stop if a compaction is
+// due before step j + 1, with step j's normalise pass still to run (the host runs it fused
+// with the packing). On stop, record j, the active count the compaction test read, the
+// active count entering the next step, and where the loop stopped (0 before the step, 1
+// after its finalize) in saved[0..3], and park *step at k_max + 1.
 void launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, int32_t* step, const int32_t* act_count,
-                      int32_t* saved, const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag);
+                      int32_t* saved, const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag,
+                      int after_finalize);
 
 struct InitArgs {
     int64_t n, ld;

@@ -362,6 +362,24 @@ void launch_finalize(cudaStream_t st, const FinArgs& a)
 }
 
 // ------------------------------------------------------------- normalise
+// One element of q_{i+1} = (W - alpha_i q_i - c_i) * (1/beta_{i+1}); every normalise kernel
+// forms it this way, so that the packed form (k_normalize_pack) equals the plain one bit for bit.
+template <typename T>
+__device__ __forceinline__ T lanczos_next(T w, T al, T qc, T c, T ib)
+{
+    return (w - al * qc - c) * ib;
+}
+template <>
+__device__ __forceinline__ float lanczos_next<float>(float w, float al, float qc, float c, float ib)
+{
+    return __fmul_rn(__fsub_rn(__fmaf_rn(-al, qc, w), c), ib);
+}
+template <>
+__device__ __forceinline__ double lanczos_next<double>(double w, double al, double qc, double c, double ib)
+{
+    return __dmul_rn(__dsub_rn(__fma_rn(-al, qc, w), c), ib);
+}
+
 // q_{i+1} = (W - alpha_i q_i - c_i) / beta_{i+1}, written over W; optionally
 // phi += coef * q_i for the replay pass. 16-byte units; ld == 1 handled separately.
 template <typename T, bool LD1>
@@ -386,7 +404,7 @@ __global__ void __launch_bounds__(256) k_normalize(const NormArgs<T> a)
         if constexpr (LD1) {
             const T al = cf_al[0], c = cf_c[0], ib = cf_ib[0];
 #pragma unroll
-            for (int i = 0; i < V; ++i) qn[i] = (w[i] - al * qc[i] - c) * ib;
+            for (int i = 0; i < V; ++i) qn[i] = lanczos_next<T>(w[i], al, qc[i], c, ib);
             if (a.phi) {
                 const T cf = a.coef[0];
                 T ph[V];
@@ -402,7 +420,7 @@ __global__ void __launch_bounds__(256) k_normalize(const NormArgs<T> a)
             ld_plain<T, V>(c, cf_c + c0);
             ld_plain<T, V>(ib, cf_ib + c0);
 #pragma unroll
-            for (int i = 0; i < V; ++i) qn[i] = (w[i] - al[i] * qc[i] - c[i]) * ib[i];
+            for (int i = 0; i < V; ++i) qn[i] = lanczos_next<T>(w[i], al[i], qc[i], c[i], ib[i]);
             if (a.phi) {
                 T cf[V], ph[V];
                 ld_plain<T, V>(cf, a.coef + c0);
@@ -419,7 +437,7 @@ __global__ void __launch_bounds__(256) k_normalize(const NormArgs<T> a)
         const int64_t t0 = units * V;
         for (int64_t e = t0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
             const T w = a.w_to_qnext[e], qc = a.qcur[e];
-            a.w_to_qnext[e] = (w - cf_al[0] * qc - cf_c[0]) * cf_ib[0];
+            a.w_to_qnext[e] = lanczos_next<T>(w, cf_al[0], qc, cf_c[0], cf_ib[0]);
             if (a.phi) a.phi[e] += a.coef[0] * qc;
         }
     }
@@ -464,7 +482,7 @@ __global__ void __launch_bounds__(256) k_normalize_pot(const NormArgs<T> a)
         T qn[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            qn[i] = (w[i] - al[i] * qc[i] - c[i]) * ib[i];
+            qn[i] = lanczos_next<T>(w[i], al[i], qc[i], c[i], ib[i]);
             pv[i] = qc[i] + lam[i] * pv[i];
             xv[i] += mu[i] * pv[i];
         }
@@ -495,41 +513,54 @@ __global__ void k_step_advance(int32_t* step, int limit)
 
 void launch_step_advance(cudaStream_t st, int32_t* step, int limit) { k_step_advance<<<1, 1, 0, st>>>(step, limit); }
 
-// Condition of the device-resident step loop (a conditional while node of a CUDA graph): with
-// j steps done, go on while pairs are active, k_max is not reached and no column compaction is
-// due. The compaction test reads the count `lag` steps back (active pairs fit in half the
-// width), as rd_query's host polls do, so that both pack the columns at the same step. To stop,
-// record j and the active counts after j - 1 and j steps in saved[0..2] (one read for the
-// host) and move the step index to the sentinel k_max + 1, whose active count is always 0, so
-// that the remaining kernels of the loop body return at once; an index already at the
-// sentinel stays there.
+// Conditions of the device-resident step loop (a conditional while node of a CUDA graph).
+// Before step j (j steps done): go on while pairs are active, k_max is not reached and no
+// column compaction is due. After step j's finalize: stop when a compaction is due before step
+// j + 1 (and step j + 1 is to run), leaving step j's normalise pass to the host, which runs it
+// fused with the packing. The compaction test reads the count `lag` steps back (active pairs
+// fit in half the width), as rd_query's host polls do, so that both pack the columns at the
+// same step; it is skipped before step *compact_from (the host moves that past a step where it
+// packed, or found no narrower layout). To stop, record j, the count the test read, the count
+// entering the next step, and where the loop stopped in saved[0..3] (one read for the host),
+// and move the step index to the sentinel k_max + 1, whose active count is always 0, so that
+// the remaining kernels of the loop body return at once; an index at the sentinel stays there.
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, int32_t* step, const int32_t* act_count, int32_t* saved,
-                            const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag)
+                            const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag,
+                            int after_finalize)
 {
     const int j = *step;
     if (j > k_max) {
         cudaGraphSetConditional(h, 0);
         return;
     }
-    const int act = act_count[j];
-    // compaction is tested from step *compact_from on (the host moves it past a step where
-    // packing found no narrower layout)
-    const bool compact_due = compact_check && j >= lag + 1 && j >= *compact_from && ld > 16 &&
-                             (int64_t)act_count[j - lag] * 2 <= ld;
-    const bool go = act > 0 && j < k_max && !compact_due;
-    if (!go) {
-        saved[0] = j;
-        saved[1] = j > 0 ? act_count[j - 1] : act;
-        saved[2] = act;
-        *step = k_max + 1;
+    const int jn = j + after_finalize;  // the step the test is for
+    const int act = act_count[jn];
+    const bool compact_due = compact_check && jn >= lag + 1 && jn >= *compact_from && ld > 16 &&
+                             (int64_t)act_count[jn - lag] * 2 <= ld;
+    bool stop;
+    if (after_finalize) {
+        stop = compact_due && act > 0 && jn < k_max;  // otherwise the next condition decides
+    } else {
+        stop = act == 0 || j >= k_max || compact_due;
     }
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (stop) {
+        saved[0] = j;
+        saved[1] = act_count[jn >= lag ? jn - lag : 0];
+        saved[2] = act;
+        saved[3] = after_finalize;
+        *step = k_max + 1;
+        cudaGraphSetConditional(h, 0);
+    } else if (!after_finalize) {
+        cudaGraphSetConditional(h, 1);
+    }
 }
 
 void launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, int32_t* step, const int32_t* act_count,
-                      int32_t* saved, const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag)
+                      int32_t* saved, const int32_t* compact_from, int k_max, int64_t ld, int compact_check, int lag,
+                      int after_finalize)
 {
-    k_loop_cond<<<1, 1, 0, st>>>(h, step, act_count, saved, compact_from, k_max, ld, compact_check, lag);
+    k_loop_cond<<<1, 1, 0, st>>>(h, step, act_count, saved, compact_from, k_max, ld, compact_check, lag,
+                                 after_finalize);
 }
 
 // ------------------------------------------------------- sparse first step
@@ -656,6 +687,64 @@ void launch_step0_df64(cudaStream_t st, const Step0Args<df64>& a) { launch_step0
 void launch_normalize_f32(int grid, cudaStream_t st, const NormArgs<float>& a) { launch_norm<float>(grid, st, a); }
 void launch_normalize_f64(int grid, cudaStream_t st, const NormArgs<double>& a) { launch_norm<double>(grid, st, a); }
 void launch_normalize_df64(int grid, cudaStream_t st, const NormArgs<df64>& a) { launch_norm<df64>(grid, st, a); }
+
+// The normalise pass of the step after which the active columns are packed (a column
+// compaction), fused with the packing: new column d takes old column o = old_slot[d] (-1:
+// zero), and both q_{i+1} (formed from W, q_i and the step's coefficients as k_normalize
+// forms it) and q_i are written in the packed layout. One read of W and q_i and one write of
+// each packed block, against a normalise pass plus a packing pass that reads both full blocks
+// again. Thread t keeps one 16-byte column unit (its slots and coefficients in registers)
+// and walks the rows t / units, + rows_per_pass, ...
+template <typename T>
+__global__ void __launch_bounds__(256) k_normalize_pack(const NormPackArgs<T> a)
+{
+    constexpr int V = 16 / (int)sizeof(T);
+    const int64_t units = a.ld_new / V;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t rows_per_pass = (int64_t)gridDim.x * blockDim.x / units;
+    const int64_t r0 = t / units;
+    if (r0 >= rows_per_pass) return;
+    const int64_t cu = t % units;
+    int o[V];
+    T al[V], c[V], ib[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        o[i] = a.old_slot[cu * V + i];
+        const int os = o[i] >= 0 ? o[i] : 0;
+        al[i] = a.cf[a.ld_old + os];
+        c[i] = a.cf[2 * a.ld_old + os];
+        ib[i] = a.cf[3 * a.ld_old + os];
+    }
+    for (int64_t u = r0; u < a.n; u += rows_per_pass) {
+        const T* wr = a.w + u * a.ld_old;
+        const T* qr = a.qcur + u * a.ld_old;
+        T qn[V], qc[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            if (o[i] >= 0) {
+                qc[i] = qr[o[i]];
+                qn[i] = lanczos_next<T>(wr[o[i]], al[i], qc[i], c[i], ib[i]);
+            } else {
+                qc[i] = T(0);
+                qn[i] = T(0);
+            }
+        }
+        st_plain<T, V>(a.qnext_new + u * a.ld_new + cu * V, qn);
+        st_plain<T, V>(a.qcur_new + u * a.ld_new + cu * V, qc);
+    }
+}
+
+template <typename T>
+static bool launch_npack(int grid, cudaStream_t st, const NormPackArgs<T>& a)
+{
+    constexpr int64_t V = 16 / (int64_t)sizeof(T);
+    if (a.ld_new % V != 0 || (int64_t)grid * 256 < a.ld_new / V) return false;
+    k_normalize_pack<T><<<grid, 256, 0, st>>>(a);
+    return true;
+}
+bool launch_normalize_pack_f32(int grid, cudaStream_t st, const NormPackArgs<float>& a) { return launch_npack(grid, st, a); }
+bool launch_normalize_pack_f64(int grid, cudaStream_t st, const NormPackArgs<double>& a) { return launch_npack(grid, st, a); }
+bool launch_normalize_pack_df64(int grid, cudaStream_t st, const NormPackArgs<df64>& a) { return launch_npack(grid, st, a); }
 
 // Double-float copy of an FP64 array (degrees and their inverses for RD_MODE_DF64).
 __global__ void k_split_df(int64_t n, const double* __restrict__ src, df64* __restrict__ dst)
@@ -927,6 +1016,12 @@ __global__ void __launch_bounds__(256) k_compact_cols_v(const CompactArgs a)
         st_plain<T, V>(d0 + u * a.ld_new + cu * V, x0);
         st_plain<T, V>(d1 + u * a.ld_new + cu * V, x1);
     }
+}
+
+void launch_compact_map(cudaStream_t st, const CompactArgs& a)
+{
+    if (a.elem_size == 8) k_compact_map<double><<<1, 1024, 0, st>>>(a);
+    else k_compact_map<float><<<1, 1024, 0, st>>>(a);
 }
 
 void launch_compact(cudaStream_t st, int grid, const CompactArgs& a)
