@@ -775,6 +775,29 @@ static bool sparse_first_step(const RunCtx& c)
 static void launch_step0_t(cudaStream_t st, const Step0Args<float>& a) { launch_step0_f32(st, a); }
 static void launch_step0_t(cudaStream_t st, const Step0Args<double>& a) { launch_step0_f64(st, a); }
 static void launch_step0_t(cudaStream_t st, const Step0Args<df64>& a) { launch_step0_df64(st, a); }
+static void launch_norm0_t(cudaStream_t st, const Step0NormArgs<float>& a) { launch_normalize_step0_f32(st, a); }
+static void launch_norm0_t(cudaStream_t st, const Step0NormArgs<double>& a) { launch_normalize_step0_f64(st, a); }
+static void launch_norm0_t(cudaStream_t st, const Step0NormArgs<df64>& a) { launch_normalize_step0_df64(st, a); }
+
+// Step 0's normalise pass after the sparse first step (finalized without deflation): only the
+// rows next to s and t of each column.
+template <typename T>
+static void enqueue_normalize_step0(RunCtx& c)
+{
+    Step0NormArgs<T> a{};
+    a.n = c.g->n;
+    a.ld = c.cur.ld;
+    a.npairs = (int)c.P;
+    a.row_ptr = c.g->row_ptr;
+    a.col = c.g->col;
+    a.s = c.b.s;
+    a.t = c.b.t;
+    a.q1 = static_cast<const T*>(c.b.q[1]);
+    a.w = static_cast<T*>(c.b.q[0]);
+    a.cf = coef_block<T>(c, 0);
+    launch_norm0_t(c.st, a);
+    ++c.launches;
+}
 
 template <typename T>
 static void enqueue_step0(RunCtx& c, bool reduce)
@@ -1242,6 +1265,14 @@ static rd_status run_forward(RunCtx& c)
             fa.ld = c.cur.ld;
             fa.tp = c.cur.cfg.tp();
             fa.nblocks = sparse ? 1 : c.cur.grid_main;
+            // after the sparse first step the deflated component is left out (it vanishes in
+            // exact arithmetic), so q_2 vanishes away from s, t and their neighbours and the
+            // normalise pass of a query touches only those rows (the potential's pass, which
+            // also updates its direction vectors, stays dense)
+            const bool undeflated = sparse && !c.lazy_walk;
+            const bool sparse_norm = undeflated && !c.pot_x;
+            const int deflate = fa.deflate;
+            if (undeflated) fa.deflate = 0;
             if (c.compact) {
                 fa.slot_pair = c.slot_sel >= 0 ? c.b.slot_pair[c.slot_sel] : nullptr;
                 fa.cf_step = c.b.cf_cur[c.cf_sel];
@@ -1253,7 +1284,9 @@ static rd_status run_forward(RunCtx& c)
             }
             launch_finalize(c.st, fa);
             ++c.launches;
-            enqueue_normalize<T>(c, j, false);
+            fa.deflate = deflate;
+            if (sparse_norm) enqueue_normalize_step0<T>(c);
+            else enqueue_normalize<T>(c, j, false);
             if (c.graph) {  // graph-replayed steps read the step index from device memory
                 launch_step_advance(c.st, c.b.step_dev, c.pl.k_max);
                 ++c.launches;

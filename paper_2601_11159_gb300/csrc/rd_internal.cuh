@@ -424,6 +424,23 @@ struct Step0Args {
     T* wout;                      // W, written over the zeroed q_0 block
     double* block_part;           // [slab][1][3][TP]: each column's sums as one block (nullable)
 };
+// Step 0's normalise pass after the sparse first step, undeflated: only the rows of
+// N(s) ∪ N(t) ∪ {s, t} of each column are written (k_normalize_step0).
+template <typename T>
+struct Step0NormArgs {
+    int64_t n, ld;
+    int npairs;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int32_t* s;
+    const int32_t* t;
+    const T* q1;                  // q_1 block
+    T* w;                         // in: W_1 (k_step0_sparse's output), out: q_2 (in place)
+    const T* cf;                  // [4][ld]: beta_1, alpha_1, c_1 (0), 1/beta_2
+};
+void launch_normalize_step0_f32(cudaStream_t st, const Step0NormArgs<float>& a);
+void launch_normalize_step0_f64(cudaStream_t st, const Step0NormArgs<double>& a);
+void launch_normalize_step0_df64(cudaStream_t st, const Step0NormArgs<df64>& a);
 void launch_step0_f32(cudaStream_t st, const Step0Args<float>& a);
 void launch_step0_f64(cudaStream_t st, const Step0Args<double>& a);
 void launch_step0_df64(cudaStream_t st, const Step0Args<df64>& a);

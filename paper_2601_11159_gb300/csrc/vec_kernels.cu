@@ -680,6 +680,58 @@ static void launch_step0(cudaStream_t st, const Step0Args<T>& a)
 {
     if (a.npairs > 0) k_step0_sparse<T><<<a.npairs, 256, 0, st>>>(a);
 }
+// Step 0's normalise pass after the sparse first step, without the deflation term (c_1 = 0:
+// the deflated component sum(d W_1) = d_s q_1[s] + d_t q_1[t] vanishes in exact arithmetic).
+// W_1 is nonzero only on N(s) ∪ N(t) and q_1 only on {s, t}, so q_2 = (W_1 - alpha_1 q_1) /
+// beta_2 vanishes elsewhere, where the dense pass would write the zeros the block already
+// holds. One CTA per column updates each row of that union once, in place, with the same
+// arithmetic as k_normalize: N(L) of the endpoint of larger degree, then N(S) minus N(L)
+// (binary search in the sorted row L), then s and t unless they are adjacent (then each is
+// in the other's row). Needs rows strictly increasing in column (as k_step0_sparse does).
+template <typename T>
+__global__ void __launch_bounds__(256) k_normalize_step0(const Step0NormArgs<T> a)
+{
+    const int p = blockIdx.x;
+    const int32_t s = a.s[p], t = a.t[p];
+    if (s < 0 || (int64_t)s >= a.n || t < 0 || (int64_t)t >= a.n || s == t) return;  // the column is zero
+    const int64_t ld = a.ld;
+    const T al = a.cf[ld + p], c = a.cf[2 * ld + p], ib = a.cf[3 * ld + p];
+    auto upd = [&](int32_t u) {
+        T* wp = a.w + (int64_t)u * ld + p;
+        *wp = lanczos_next<T>(*wp, al, a.q1[(int64_t)u * ld + p], c, ib);
+    };
+    const int64_t ds_n = a.row_ptr[s + 1] - a.row_ptr[s], dt_n = a.row_ptr[t + 1] - a.row_ptr[t];
+    const int32_t L = ds_n >= dt_n ? s : t, S = ds_n >= dt_n ? t : s;
+    const int64_t lb = a.row_ptr[L], le = a.row_ptr[L + 1];
+    const int64_t sb = a.row_ptr[S], se = a.row_ptr[S + 1];
+    auto in_row_L = [&](int32_t u) {
+        int64_t lo = lb, hi = le;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(a.col + mid) < u) lo = mid + 1; else hi = mid;
+        }
+        return lo < le && __ldg(a.col + lo) == u;
+    };
+    for (int64_t e = lb + threadIdx.x; e < le; e += blockDim.x) upd(__ldg(a.col + e));
+    for (int64_t e = sb + threadIdx.x; e < se; e += blockDim.x) {
+        const int32_t u = __ldg(a.col + e);
+        if (!in_row_L(u)) upd(u);
+    }
+    if (threadIdx.x == 0 && !in_row_L(S)) {
+        upd(s);
+        upd(t);
+    }
+}
+
+template <typename T>
+static void launch_norm0(cudaStream_t st, const Step0NormArgs<T>& a)
+{
+    if (a.npairs > 0) k_normalize_step0<T><<<a.npairs, 256, 0, st>>>(a);
+}
+void launch_normalize_step0_f32(cudaStream_t st, const Step0NormArgs<float>& a) { launch_norm0<float>(st, a); }
+void launch_normalize_step0_f64(cudaStream_t st, const Step0NormArgs<double>& a) { launch_norm0<double>(st, a); }
+void launch_normalize_step0_df64(cudaStream_t st, const Step0NormArgs<df64>& a) { launch_norm0<df64>(st, a); }
+
 void launch_step0_f32(cudaStream_t st, const Step0Args<float>& a) { launch_step0<float>(st, a); }
 void launch_step0_f64(cudaStream_t st, const Step0Args<double>& a) { launch_step0<double>(st, a); }
 void launch_step0_df64(cudaStream_t st, const Step0Args<df64>& a) { launch_step0<df64>(st, a); }

@@ -756,8 +756,13 @@ def test_double_float_mode_batched_chunglu(rd):
     G = rd.Graph.from_csr(g)
     ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=300, stop_tol=1e-15, threads=0)
     res = G.query(s, t, mode="df64", k_max=300, rel_tol=0.0, resid_tol=1e-11)
-    assert G.last_stats()["compactions"] >= 1
+    st = G.last_stats()
+    assert st["compactions"] >= 1 and st["device_loop"] == 1
     assert rel(res.r, ref).max() < FP64_TOL
+    # the device loop packs with the fused normalise pass (8-byte elements): bitwise the
+    # normalise pass followed by the separate packing of the host-driven loop
+    hl = G.query(s, t, mode="df64", k_max=300, rel_tol=0.0, resid_tol=1e-11, device_loop=False)
+    assert np.array_equal(hl.r, res.r) and np.array_equal(hl.iters, res.iters)
     r64 = G.query(s, t, mode="fp64", k_max=300, rel_tol=0.0, resid_tol=1e-11).r
     assert rel(res.r, r64).max() < 1e-10
     gd, rd_ = G.edge_grad(s[:4], t[:4], None, mode="df64", k_max=300, rel_tol=0.0, resid_tol=1e-11)
