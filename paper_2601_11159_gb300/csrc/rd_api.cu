@@ -408,9 +408,9 @@ static SpmmCfg pick_cfg(const rd_graph* g, int64_t P, const rd_query_opts& o, bo
         c.vec = 2;
         return c;
     }
-    if (o.kernel == 5) {  // async row-stream: FP32 vectors, tiles of 16 to 128 columns
-        int tpa = o.rhs_tile > 0 ? o.rhs_tile : (P <= 16 ? 16 : (P <= 32 ? 32 : (P <= 64 ? 64 : 128)));
-        c.vec = fp64 ? 2 : 4;  // an FP64 request names no instantiated tile (make_plan reports it)
+    if (o.kernel == 5) {  // async row-stream: tiles of 16 to 128 FP32 columns, 16 to 64 of 8-byte elements
+        int tpa = o.rhs_tile > 0 ? o.rhs_tile : (P <= 16 ? 16 : (P <= 32 ? 32 : (P <= 64 || fp64 ? 64 : 128)));
+        c.vec = fp64 ? 2 : 4;
         c.gs = std::max(1, tpa / c.vec);
         c.nzl = 1;
         c.kind = 3;
@@ -500,6 +500,7 @@ struct Buffers {
     int32_t* step_dev;        // step index of graph-replayed steps (zeroed per query)
     int32_t* loop_saved;      // [4]: where the device-resident loop stopped (see launch_loop_cond)
     int32_t* loop_cfrom;      // first step at which the loop tests for a column compaction
+    uint32_t* row_mask;       // n x ld bits: entries of q_2 the sparse first normalise pass wrote
     // gradient / potential
     void* phi;
     void* pvec;               // n x ld0: direction vectors of the potential's direct update
@@ -559,6 +560,8 @@ static size_t carve(Carver& c, const rd_graph* g, const Plan& pl, int64_t P, boo
     b->step_dev = c.take<int32_t>(1);
     b->loop_saved = c.take<int32_t>(4);
     b->loop_cfrom = c.take<int32_t>(1);
+    // queries on graphs that take the sparse first step (rows sorted, symmetric)
+    b->row_mask = (!grad && g->rows_sorted_sym) ? c.take<uint32_t>((n * ld + 31) / 32) : nullptr;
     b->xcf = grad ? c.take<char>(K * 2 * ld * pl.elem) : nullptr;
     c.off = (c.off + 255) & ~size_t(255);
     b->state_bytes_end = c.off;
@@ -772,15 +775,33 @@ static bool sparse_first_step(const RunCtx& c)
     return c.g->rows_sorted_sym && !c.lazy_walk && (c.o.flags & RD_Q_DENSE_FIRST) == 0;
 }
 
+// The first step's normalise pass in two sparse-aware parts (k_normalize_step0 + fill): for
+// queries (the potential's pass also updates its direction vectors), with the row mask carved
+// and whole 16-byte units per row.
+static bool sparse_norm_ok(const RunCtx& c)
+{
+    return !c.pot_x && !c.lazy_walk && c.b.row_mask && c.cur.ld % (16 / (int64_t)c.cur.elem) == 0;
+}
+
 static void launch_step0_t(cudaStream_t st, const Step0Args<float>& a) { launch_step0_f32(st, a); }
 static void launch_step0_t(cudaStream_t st, const Step0Args<double>& a) { launch_step0_f64(st, a); }
 static void launch_step0_t(cudaStream_t st, const Step0Args<df64>& a) { launch_step0_df64(st, a); }
-static void launch_norm0_t(cudaStream_t st, const Step0NormArgs<float>& a) { launch_normalize_step0_f32(st, a); }
-static void launch_norm0_t(cudaStream_t st, const Step0NormArgs<double>& a) { launch_normalize_step0_f64(st, a); }
-static void launch_norm0_t(cudaStream_t st, const Step0NormArgs<df64>& a) { launch_normalize_step0_df64(st, a); }
+static void launch_norm0_t(int grid, cudaStream_t st, const Step0NormArgs<float>& a)
+{
+    launch_normalize_step0_f32(grid, st, a);
+}
+static void launch_norm0_t(int grid, cudaStream_t st, const Step0NormArgs<double>& a)
+{
+    launch_normalize_step0_f64(grid, st, a);
+}
+static void launch_norm0_t(int grid, cudaStream_t st, const Step0NormArgs<df64>& a)
+{
+    launch_normalize_step0_df64(grid, st, a);
+}
 
-// Step 0's normalise pass after the sparse first step (finalized without deflation): only the
-// rows next to s and t of each column.
+// Step 0's normalise pass after the sparse first step: the rows next to s and t of each column
+// (k_normalize_step0), then every other entry, whose value is the same per column
+// (k_normalize_step0_fill); bit for bit the dense pass.
 template <typename T>
 static void enqueue_normalize_step0(RunCtx& c)
 {
@@ -795,8 +816,9 @@ static void enqueue_normalize_step0(RunCtx& c)
     a.q1 = static_cast<const T*>(c.b.q[1]);
     a.w = static_cast<T*>(c.b.q[0]);
     a.cf = coef_block<T>(c, 0);
-    launch_norm0_t(c.st, a);
-    ++c.launches;
+    a.mask = c.b.row_mask;
+    launch_norm0_t(c.cur.grid_norm, c.st, a);
+    c.launches += 2;
 }
 
 template <typename T>
@@ -827,7 +849,9 @@ static void enqueue_step0(RunCtx& c, bool reduce)
 static void enqueue_init(RunCtx& c, bool replay)
 {
     const int64_t vbytes = c.g->n * c.cur.ld * (int64_t)c.cur.elem;
-    cudaMemsetAsync(c.b.q[0], 0, vbytes, c.st);
+    // after the sparse first step the normalise pass writes every entry of the q_0 block
+    // (k_normalize_step0 and its fill) and nothing reads it before: no zeros needed there
+    if (replay || !sparse_first_step(c) || !sparse_norm_ok(c)) cudaMemsetAsync(c.b.q[0], 0, vbytes, c.st);
     cudaMemsetAsync(c.b.q[1], 0, vbytes, c.st);
     InitArgs a{};
     a.n = c.g->n;
@@ -1265,14 +1289,7 @@ static rd_status run_forward(RunCtx& c)
             fa.ld = c.cur.ld;
             fa.tp = c.cur.cfg.tp();
             fa.nblocks = sparse ? 1 : c.cur.grid_main;
-            // after the sparse first step the deflated component is left out (it vanishes in
-            // exact arithmetic), so q_2 vanishes away from s, t and their neighbours and the
-            // normalise pass of a query touches only those rows (the potential's pass, which
-            // also updates its direction vectors, stays dense)
-            const bool undeflated = sparse && !c.lazy_walk;
-            const bool sparse_norm = undeflated && !c.pot_x;
-            const int deflate = fa.deflate;
-            if (undeflated) fa.deflate = 0;
+            const bool sparse_norm = sparse && sparse_norm_ok(c);
             if (c.compact) {
                 fa.slot_pair = c.slot_sel >= 0 ? c.b.slot_pair[c.slot_sel] : nullptr;
                 fa.cf_step = c.b.cf_cur[c.cf_sel];
@@ -1284,7 +1301,6 @@ static rd_status run_forward(RunCtx& c)
             }
             launch_finalize(c.st, fa);
             ++c.launches;
-            fa.deflate = deflate;
             if (sparse_norm) enqueue_normalize_step0<T>(c);
             else enqueue_normalize<T>(c, j, false);
             if (c.graph) {  // graph-replayed steps read the step index from device memory
@@ -1463,12 +1479,11 @@ static std::vector<SpmmCfg> tune_candidates(const rd_graph* g, int64_t width, bo
             if (gs * z <= 32)
                 for (int o : {0, 1}) add(vec, gs, z, 0, o);
     }
-    // async row-stream (FP32 vectors): column slabs of 16 to 128 columns, down to an eighth
-    // of the width (narrow slabs keep the gathered slab in L2)
-    // async row-stream (FP32 vectors): column slabs of 16 to 128 columns
-    if (!fp64)
-        for (int64_t tp = std::max<int64_t>(16, width / 8); tp <= std::min<int64_t>(width, 128); tp <<= 1)
-            add(4, (int)(tp / 4), 1, 3, 0);
+    // async row-stream: column slabs of 16 to 128 FP32 columns (16 to 64 of 8-byte elements),
+    // down to an eighth of the width
+    const int avec = fp64 ? 2 : 4;
+    for (int64_t tp = std::max<int64_t>(16, width / 8); tp <= std::min<int64_t>(width, 32 * avec); tp <<= 1)
+        add(avec, (int)(tp / avec), 1, 3, 0);
     return v;
 }
 

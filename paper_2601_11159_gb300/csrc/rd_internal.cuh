@@ -424,8 +424,9 @@ struct Step0Args {
     T* wout;                      // W, written over the zeroed q_0 block
     double* block_part;           // [slab][1][3][TP]: each column's sums as one block (nullable)
 };
-// Step 0's normalise pass after the sparse first step, undeflated: only the rows of
-// N(s) ∪ N(t) ∪ {s, t} of each column are written (k_normalize_step0).
+// Step 0's normalise pass after the sparse first step, in two parts: the rows of
+// N(s) ∪ N(t) ∪ {s, t} of each column (k_normalize_step0, marking them in `mask`), then every
+// other entry (k_normalize_step0_fill), where W_1 and q_1 are zero.
 template <typename T>
 struct Step0NormArgs {
     int64_t n, ld;
@@ -435,12 +436,13 @@ struct Step0NormArgs {
     const int32_t* s;
     const int32_t* t;
     const T* q1;                  // q_1 block
-    T* w;                         // in: W_1 (k_step0_sparse's output), out: q_2 (in place)
-    const T* cf;                  // [4][ld]: beta_1, alpha_1, c_1 (0), 1/beta_2
+    T* w;                         // in: W_1 on those rows (k_step0_sparse's output), out: q_2
+    const T* cf;                  // [4][ld]: beta_1, alpha_1, c_1, 1/beta_2
+    uint32_t* mask;               // n x ld bits, zero on entry: the entries the first part wrote
 };
-void launch_normalize_step0_f32(cudaStream_t st, const Step0NormArgs<float>& a);
-void launch_normalize_step0_f64(cudaStream_t st, const Step0NormArgs<double>& a);
-void launch_normalize_step0_df64(cudaStream_t st, const Step0NormArgs<df64>& a);
+void launch_normalize_step0_f32(int grid, cudaStream_t st, const Step0NormArgs<float>& a);
+void launch_normalize_step0_f64(int grid, cudaStream_t st, const Step0NormArgs<double>& a);
+void launch_normalize_step0_df64(int grid, cudaStream_t st, const Step0NormArgs<df64>& a);
 void launch_step0_f32(cudaStream_t st, const Step0Args<float>& a);
 void launch_step0_f64(cudaStream_t st, const Step0Args<double>& a);
 void launch_step0_df64(cudaStream_t st, const Step0Args<df64>& a);

@@ -947,20 +947,25 @@ __device__ __forceinline__ float4 lds_f4(uint32_t a)
     return v;
 }
 
-template <int GS>
+// elements of T in one 16-byte lane slot: 4 FP32, 2 FP64 or double-float
+template <typename T>
+inline constexpr int kAsyncVec = 16 / (int)sizeof(T);
+
+template <typename T, int GS>
 constexpr size_t async_smem_bytes()
 {
-    return (size_t)kWarps * kAsyncDepth * 32 * 16 + (size_t)kWarps * (4 * GS) * 8;
+    return (size_t)kWarps * kAsyncDepth * 32 * 16 + (size_t)kWarps * (kAsyncVec<T> * GS) * 8;
 }
 
-// Column indices (as row offsets in float4 units) and weights of the D nonzeros of one
+// Column indices (as row offsets in 16-byte units) and weights of the D nonzeros of one
 // round starting at `base`: lane gl holds positions gl + h GS (h < NH) of the round.
 template <int GS, bool WEIGHTED>
 struct AsyncRound {
     static constexpr int NH = (kAsyncDepth + GS - 1) / GS;
     uint32_t off[NH];
     float w[NH];
-    __device__ __forceinline__ void load(const StepArgs<float>& a, int base, int end, int gl, uint32_t ldv)
+    template <class Args>
+    __device__ __forceinline__ void load(const Args& a, int base, int end, int gl, uint32_t ldv)
     {
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
@@ -989,9 +994,35 @@ struct AsyncRound {
     }
 };
 
-// acc += w * x (or acc += x unweighted) on the four columns of a lane
+// acc += w * x (or acc += x unweighted) on the columns of a lane slot (16 bytes as read from
+// the ring): four FP32, two FP64 or two double-float (each as hi, lo)
 template <bool WEIGHTED>
-__device__ __forceinline__ void acc_add4(float (&acc)[4], const float4& x, float wv)
+__device__ __forceinline__ void acc_add_slot(double (&acc)[2], const float4& x, float wv)
+{
+    const double x0 = __hiloint2double(__float_as_int(x.y), __float_as_int(x.x));
+    const double x1 = __hiloint2double(__float_as_int(x.w), __float_as_int(x.z));
+    if constexpr (WEIGHTED) {
+        acc[0] = fma((double)wv, x0, acc[0]);
+        acc[1] = fma((double)wv, x1, acc[1]);
+    } else {
+        acc[0] += x0;
+        acc[1] += x1;
+    }
+}
+template <bool WEIGHTED>
+__device__ __forceinline__ void acc_add_slot(df64 (&acc)[2], const float4& x, float wv)
+{
+    const df64 x0(x.x, x.y, 0), x1(x.z, x.w, 0);
+    if constexpr (WEIGHTED) {
+        acc_mul_add_w(acc[0], wv, x0);
+        acc_mul_add_w(acc[1], wv, x1);
+    } else {
+        acc_add(acc[0], x0);
+        acc_add(acc[1], x1);
+    }
+}
+template <bool WEIGHTED>
+__device__ __forceinline__ void acc_add_slot(float (&acc)[4], const float4& x, float wv)
 {
     if constexpr (WEIGHTED) {
         acc[0] = fmaf(wv, x.x, acc[0]);
@@ -1010,9 +1041,10 @@ __device__ __forceinline__ void acc_add4(float (&acc)[4], const float4& x, float
 // `enter(e)` runs before nonzero e is added when e may open a new row (it closes the rows
 // that end there: row epilogues) and returns the end of the segment that e is in (the first
 // nonzero of the next row); each segment is then consumed without a boundary test per nonzero.
-template <int GS, bool WEIGHTED, class Enter>
-__device__ __forceinline__ void async_stream(const StepArgs<float>& a, const float* q, uint32_t ldv, int eb, int ee,
-                                             uint32_t ring, int gl, unsigned mask, float (&acc)[4], Enter&& enter)
+template <typename T, int GS, bool WEIGHTED, class Enter>
+__device__ __forceinline__ void async_stream(const StepArgs<T>& a, const T* q, uint32_t ldv, int eb, int ee,
+                                             uint32_t ring, int gl, unsigned mask, T (&acc)[kAsyncVec<T>],
+                                             Enter&& enter)
 {
     constexpr int D = kAsyncDepth;
     constexpr uint32_t SS = 32 * 16;  // slot stride: one float4 per lane of the warp
@@ -1022,7 +1054,7 @@ __device__ __forceinline__ void async_stream(const StepArgs<float>& a, const flo
     nxt.load(a, eb + D, ee, gl, ldv);
     for (int u = 0; u < D; ++u) {
         const uint32_t o = __shfl_sync(mask, cur.off_at(u), u % GS, GS);
-        if (eb + u < ee) cp_async16(ring + u * SS, q + (size_t)o * 4);
+        if (eb + u < ee) cp_async16(ring + u * SS, reinterpret_cast<const char*>(q) + (size_t)o * 16);
         cp_async_commit();
     }
     for (int base = eb; base < ee; base += D) {
@@ -1035,8 +1067,8 @@ __device__ __forceinline__ void async_stream(const StepArgs<float>& a, const flo
             const uint32_t o = __shfl_sync(mask, nxt.off_at(u), u % GS, GS);
             cp_async_wait<D - 1>();
             const float4 x = lds_f4(ring + u * SS);
-            acc_add4<WEIGHTED>(acc, x, wv);
-            if (u < refill) cp_async16(ring + u * SS, q + (size_t)o * 4);
+            acc_add_slot<WEIGHTED>(acc, x, wv);
+            if (u < refill) cp_async16(ring + u * SS, reinterpret_cast<const char*>(q) + (size_t)o * 16);
             cp_async_commit();
         };
         for (int u = 0; u < cnt;) {
@@ -1050,10 +1082,11 @@ __device__ __forceinline__ void async_stream(const StepArgs<float>& a, const flo
 }
 
 // Heavy-row pre-pass of the async kernel: the chunk partials heavy_part[chunk, slab].
-template <int GS, bool WEIGHTED>
-__global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async_heavy(const StepArgs<float> a)
+template <typename T, int GS, bool WEIGHTED>
+__global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async_heavy(const StepArgs<T> a)
 {
-    constexpr int TP = 4 * GS;
+    constexpr int V = kAsyncVec<T>;
+    constexpr int TP = V * GS;
     constexpr int NG = 32 / GS;
     extern __shared__ __align__(16) float smem_f[];
     if (step_inactive(a)) return;
@@ -1064,15 +1097,19 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async_heavy(cons
     const int64_t ngroups = (int64_t)gridDim.x * kWarps * NG;
     const int64_t gid = ((int64_t)blockIdx.x * kWarps + warp) * NG + grp;
     const int nslab = (int)(a.ld / TP);
-    const uint32_t ldv = (uint32_t)(a.ld / 4);
+    const uint32_t ldv = (uint32_t)(a.ld / V);
     for (int slab = 0; slab < nslab; ++slab) {
-        const int64_t c0 = (int64_t)slab * TP + gl * 4;
-        const float* q = a.qcur + c0;
+        const int64_t c0 = (int64_t)slab * TP + gl * V;
+        const T* q = a.qcur + c0;
         for (int64_t ch = gid; ch < a.n_chunks; ch += ngroups) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            async_stream<GS, WEIGHTED>(a, q, ldv, a.chunk_beg[ch], a.chunk_end[ch], ring, gl, mask, acc,
-                                       [](int) { return INT_MAX; });
-            st_plain<float, 4>(a.heavy_part + ch * a.ld + c0, acc);
+            T acc[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) acc[i] = T(0);
+            async_stream<T, GS, WEIGHTED>(a, q, ldv, a.chunk_beg[ch], a.chunk_end[ch], ring, gl, mask, acc,
+                                          [](int) { return INT_MAX; });
+#pragma unroll
+            for (int i = 0; i < V; ++i) acc_finish(acc[i]);
+            st_plain<T, V>(a.heavy_part + ch * a.ld + c0, acc);
         }
     }
 }
@@ -1080,10 +1117,11 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async_heavy(cons
 // Main kernel: W = D^{-1} W_adj q_i - beta_i q_{i-1} over q_{i-1}, and the block partials of
 // sum d W q_i, sum d W^2, sum d W per column (slab by slab). Row groups take the tasks
 // grid-strided; a task of light rows is one stream of nonzeros through the ring.
-template <int GS, bool WEIGHTED>
-__global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const StepArgs<float> a)
+template <typename T, int GS, bool WEIGHTED>
+__global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const StepArgs<T> a)
 {
-    constexpr int TP = 4 * GS;
+    constexpr int V = kAsyncVec<T>;
+    constexpr int TP = V * GS;
     constexpr int NG = 32 / GS;
     constexpr int PD = RD_ASYNC_PF_DIST;
     extern __shared__ __align__(16) float smem_f[];
@@ -1097,36 +1135,40 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const Step
     const int gid = (blockIdx.x * kWarps + warp) * NG + grp;
     const int nslab = (int)(a.ld / TP);
     const int64_t ld = a.ld;
-    const uint32_t ldv = (uint32_t)(ld / 4);
+    const uint32_t ldv = (uint32_t)(ld / V);
     const int ntasks = (int)a.ntasks;
 
     for (int slab = 0; slab < nslab; ++slab) {
-        const int64_t c0 = (int64_t)slab * TP + gl * 4;
-        float bt[4];
-        ld_plain<float, 4>(bt, step_cf_beta(a) + c0);
-        Acc<float> sA[4], sB[4], sC[4];
-        const float* q = a.qcur + c0;
+        const int64_t c0 = (int64_t)slab * TP + gl * V;
+        T bt[V];
+        ld_plain<T, V>(bt, step_cf_beta(a) + c0);
+        Acc<T> sA[V], sB[V], sC[V];
+        const T* q = a.qcur + c0;
         // a heavy row: the sum of its chunk partials [f, l)
         auto heavy_row = [&](int r, int f, int l) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f}, qp[4], qc[4];
-            ld_stream<float, 4>(qp, a.qprev_w + (int64_t)r * ld + c0);
-            ld_gather<float, 4>(qc, q + (int64_t)r * ld);
-            heavy_chunks_sum<float, 4, 1>(a, f, l, c0, 0, acc);
-            row_epilogue<float, 4>(a, r, c0, a.invdeg[r], a.deg[r], acc, bt, qp, qc, sA, sB, sC);
+            T acc[V], qp[V], qc[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) acc[i] = T(0);
+            ld_stream<T, V>(qp, a.qprev_w + (int64_t)r * ld + c0);
+            ld_gather<T, V>(qc, q + (int64_t)r * ld);
+            heavy_chunks_sum<T, V, 1>(a, f, l, c0, 0, acc);
+            row_epilogue<T, V>(a, r, c0, a.invdeg[r], a.deg[r], acc, bt, qp, qc, sA, sB, sC);
         };
         // light rows [r0, r1): one stream of their nonzeros
         auto light_rows = [&](int r0, int r1) {
             const int eb = (int)a.row_ptr[r0], ee = (int)a.row_ptr[r1];
-            float acc[4] = {0.f, 0.f, 0.f, 0.f}, qp[4], qc[4];
+            T acc[V], qp[V], qc[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) acc[i] = T(0);
             // row window: lane gl holds row_ptr[w0 + gl + 1], 1/d and d of row w0 + gl
             int w0 = r0;
             int my_end = (w0 + gl < r1) ? (int)a.row_ptr[w0 + gl + 1] : ee;
-            float my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : 0.f;
-            float my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : 0.f;
+            T my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : T(0);
+            T my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : T(0);
             int row = r0;
             int row_end = __shfl_sync(mask, my_end, 0, GS);
-            ld_stream<float, 4>(qp, a.qprev_w + (int64_t)row * ld + c0);
-            ld_gather<float, 4>(qc, q + (int64_t)row * ld);
+            ld_stream<T, V>(qp, a.qprev_w + (int64_t)row * ld + c0);
+            ld_gather<T, V>(qc, q + (int64_t)row * ld);
             // the own-row operands of the next PD rows into L2 (no registers held): short rows
             // end before a load from DRAM would return
 #pragma unroll
@@ -1138,28 +1180,30 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const Step
             // close the current row and open the next one
             auto next_row = [&]() {
                 const int wi = row - w0;
-                const float invd = __shfl_sync(mask, my_invd, wi, GS);
-                const float du = __shfl_sync(mask, my_deg, wi, GS);
-                row_epilogue<float, 4>(a, row, c0, invd, du, acc, bt, qp, qc, sA, sB, sC);
+                const T invd = shfl_t(mask, my_invd, wi, GS);
+                const T du = shfl_t(mask, my_deg, wi, GS);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] = 0.f;
+                for (int i = 0; i < V; ++i) acc_finish(acc[i]);
+                row_epilogue<T, V>(a, row, c0, invd, du, acc, bt, qp, qc, sA, sB, sC);
+#pragma unroll
+                for (int i = 0; i < V; ++i) acc[i] = T(0);
                 ++row;
                 if (row >= r1) return;
                 if (row - w0 >= GS) {  // refill the row window
                     w0 = row;
                     my_end = (w0 + gl < r1) ? (int)a.row_ptr[w0 + gl + 1] : ee;
-                    my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : 0.f;
-                    my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : 0.f;
+                    my_invd = (w0 + gl < r1) ? a.invdeg[w0 + gl] : T(0);
+                    my_deg = (w0 + gl < r1) ? a.deg[w0 + gl] : T(0);
                 }
                 row_end = __shfl_sync(mask, my_end, row - w0, GS);
-                ld_stream<float, 4>(qp, a.qprev_w + (int64_t)row * ld + c0);
-                ld_gather<float, 4>(qc, q + (int64_t)row * ld);
+                ld_stream<T, V>(qp, a.qprev_w + (int64_t)row * ld + c0);
+                ld_gather<T, V>(qc, q + (int64_t)row * ld);
                 if (PD > 0 && row + PD < r1) {
                     prefetch_l2(a.qprev_w + (int64_t)(row + PD) * ld + c0);
                     prefetch_l2(q + (int64_t)(row + PD) * ld);
                 }
             };
-            async_stream<GS, WEIGHTED>(a, q, ldv, eb, ee, ring, gl, mask, acc, [&](int e) {
+            async_stream<T, GS, WEIGHTED>(a, q, ldv, eb, ee, ring, gl, mask, acc, [&](int e) {
                 while (e >= row_end) next_row();
                 return row_end;
             });
@@ -1174,51 +1218,51 @@ __global__ void __launch_bounds__(kBlock, RD_ASYNC_MINB) k_spmm_async(const Step
             }
             light_rows(r0, r1);
         }
-        if (a.do_reduce) block_partials<float, 4, GS, TP>(a, sA, sB, sC, red, slab, lane, warp, gl);
+        if (a.do_reduce) block_partials<T, V, GS, TP>(a, sA, sB, sC, red, slab, lane, warp, gl);
     }
 }
 
-template <int GS>
+template <typename T, int GS>
 void async_smem_attr()
 {
-    constexpr size_t sm = async_smem_bytes<GS>();
+    constexpr size_t sm = async_smem_bytes<T, GS>();
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_spmm_async<GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_spmm_async<GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_spmm_async_heavy<GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_spmm_async_heavy<GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_spmm_async<T, GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_spmm_async<T, GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_spmm_async_heavy<T, GS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_spmm_async_heavy<T, GS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
 }
 
-template <int GS>
-bool launch_async_cfg(bool weighted, bool heavy, int grid, cudaStream_t st, const StepArgs<float>& a)
+template <typename T, int GS>
+bool launch_async_cfg(bool weighted, bool heavy, int grid, cudaStream_t st, const StepArgs<T>& a)
 {
-    constexpr size_t sm = async_smem_bytes<GS>();
-    async_smem_attr<GS>();
+    constexpr size_t sm = async_smem_bytes<T, GS>();
+    async_smem_attr<T, GS>();
     if (heavy) {
-        if (weighted) k_spmm_async_heavy<GS, true><<<grid, kBlock, sm, st>>>(a);
-        else k_spmm_async_heavy<GS, false><<<grid, kBlock, sm, st>>>(a);
+        if (weighted) k_spmm_async_heavy<T, GS, true><<<grid, kBlock, sm, st>>>(a);
+        else k_spmm_async_heavy<T, GS, false><<<grid, kBlock, sm, st>>>(a);
     } else {
-        if (weighted) k_spmm_async<GS, true><<<grid, kBlock, sm, st>>>(a);
-        else k_spmm_async<GS, false><<<grid, kBlock, sm, st>>>(a);
+        if (weighted) k_spmm_async<T, GS, true><<<grid, kBlock, sm, st>>>(a);
+        else k_spmm_async<T, GS, false><<<grid, kBlock, sm, st>>>(a);
     }
     return true;
 }
 
-template <int GS>
+template <typename T, int GS>
 int occupancy_async_cfg(bool weighted, bool heavy)
 {
     int nb = 0;
-    constexpr size_t sm = async_smem_bytes<GS>();
-    async_smem_attr<GS>();
+    constexpr size_t sm = async_smem_bytes<T, GS>();
+    async_smem_attr<T, GS>();
     if (heavy) {
-        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async_heavy<GS, true>, kBlock, sm);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async_heavy<GS, false>, kBlock, sm);
+        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async_heavy<T, GS, true>, kBlock, sm);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async_heavy<T, GS, false>, kBlock, sm);
     } else {
-        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async<GS, true>, kBlock, sm);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async<GS, false>, kBlock, sm);
+        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async<T, GS, true>, kBlock, sm);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmm_async<T, GS, false>, kBlock, sm);
     }
     return nb;
 }

@@ -39,7 +39,7 @@ bool launch_spmm_f32(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
     if (c.kind == 3) {
         if (c.vec != 4 || c.nzl != 1) return false;
 #define X(G) \
-    if (c.gs == G) return launch_async_cfg<G>(weighted, heavy, grid, st, a);
+    if (c.gs == G) return launch_async_cfg<float, G>(weighted, heavy, grid, st, a);
         RD_F32_ASYNC(X)
 #undef X
         return false;
@@ -67,7 +67,7 @@ int spmm_blocks_per_sm_f32(const SpmmCfg& c, bool weighted, bool heavy)
     if (c.kind == 3) {
         if (c.vec != 4 || c.nzl != 1) return 0;
 #define X(G) \
-    if (c.gs == G) return occupancy_async_cfg<G>(weighted, heavy);
+    if (c.gs == G) return occupancy_async_cfg<float, G>(weighted, heavy);
         RD_F32_ASYNC(X)
 #undef X
         return 0;

@@ -25,9 +25,23 @@ namespace rd {
     X(2, 32, 1)           \
     X(4, 32, 1)
 
+// async row-stream (kind 3): two 8-byte elements per 16-byte lane slot, slabs of 16 to 64 columns
+#define RD_F64_ASYNC(X) \
+    X(8)                \
+    X(16)               \
+    X(32)
+
 bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cudaStream_t st,
                      const StepArgs<double>& a)
 {
+    if (c.kind == 3) {
+        if (c.vec != 2 || c.nzl != 1) return false;
+#define X(G) \
+    if (c.gs == G) return launch_async_cfg<double, G>(weighted, heavy, grid, st, a);
+        RD_F64_ASYNC(X)
+#undef X
+        return false;
+    }
     if (c.kind == 2 && !heavy) return launch_spmv_tasks<double>(weighted, grid, st, a);
     if (c.kind == 1 && !heavy) {
 #define X(V, G) \
@@ -48,6 +62,14 @@ bool launch_spmm_f64(const SpmmCfg& c, bool weighted, bool heavy, int grid, cuda
 
 int spmm_blocks_per_sm_f64(const SpmmCfg& c, bool weighted, bool heavy)
 {
+    if (c.kind == 3) {
+        if (c.vec != 2 || c.nzl != 1) return 0;
+#define X(G) \
+    if (c.gs == G) return occupancy_async_cfg<double, G>(weighted, heavy);
+        RD_F64_ASYNC(X)
+#undef X
+        return 0;
+    }
     if (c.kind == 2 && !heavy) return occupancy_spmv_tasks<double>(weighted);
     if (c.kind == 1 && !heavy) {
 #define X(V, G) \
@@ -73,6 +95,9 @@ std::vector<SpmmCfg> spmm_configs_f64()
     v.push_back(SpmmCfg{1, 1, 1, 2});
 #define X(V, G) v.push_back(SpmmCfg{V, G, 1, 1});
     RD_F64_ROWS(X)
+#undef X
+#define X(G) v.push_back(SpmmCfg{2, G, 1, 3});
+    RD_F64_ASYNC(X)
 #undef X
     return v;
 }

@@ -680,25 +680,30 @@ static void launch_step0(cudaStream_t st, const Step0Args<T>& a)
 {
     if (a.npairs > 0) k_step0_sparse<T><<<a.npairs, 256, 0, st>>>(a);
 }
-// Step 0's normalise pass after the sparse first step, without the deflation term (c_1 = 0:
-// the deflated component sum(d W_1) = d_s q_1[s] + d_t q_1[t] vanishes in exact arithmetic).
-// W_1 is nonzero only on N(s) ∪ N(t) and q_1 only on {s, t}, so q_2 = (W_1 - alpha_1 q_1) /
-// beta_2 vanishes elsewhere, where the dense pass would write the zeros the block already
-// holds. One CTA per column updates each row of that union once, in place, with the same
-// arithmetic as k_normalize: N(L) of the endpoint of larger degree, then N(S) minus N(L)
-// (binary search in the sorted row L), then s and t unless they are adjacent (then each is
-// in the other's row). Needs rows strictly increasing in column (as k_step0_sparse does).
+// Step 0's normalise pass after the sparse first step, first part. W_1 is nonzero only on
+// N(s) ∪ N(t) and q_1 only on {s, t}; elsewhere q_2 = (W_1 - alpha_1 q_1 - c_1) / beta_2 is the
+// same value in every row of a column (left to the fill). One CTA per column updates each row
+// of that union once, in place, with k_normalize's arithmetic, and marks its entry in the
+// mask: N(L) of the endpoint of larger degree, then N(S) minus N(L) (binary search in the
+// sorted row L), then s and t unless they are adjacent (then each is in the other's row).
+// Columns whose first step wrote nothing (as k_step0_sparse decides) are left to the fill.
 template <typename T>
 __global__ void __launch_bounds__(256) k_normalize_step0(const Step0NormArgs<T> a)
 {
     const int p = blockIdx.x;
     const int32_t s = a.s[p], t = a.t[p];
-    if (s < 0 || (int64_t)s >= a.n || t < 0 || (int64_t)t >= a.n || s == t) return;  // the column is zero
     const int64_t ld = a.ld;
+    bool live = s >= 0 && (int64_t)s < a.n && t >= 0 && (int64_t)t < a.n && s != t;
+    if (live)
+        live = to_double(a.q1[(int64_t)s * ld + p]) != 0.0 || to_double(a.q1[(int64_t)t * ld + p]) != 0.0;
+    if (!live) return;  // uniform over the block
     const T al = a.cf[ld + p], c = a.cf[2 * ld + p], ib = a.cf[3 * ld + p];
-    auto upd = [&](int32_t u) {
-        T* wp = a.w + (int64_t)u * ld + p;
-        *wp = lanczos_next<T>(*wp, al, a.q1[(int64_t)u * ld + p], c, ib);
+    // w_zero: a row the first step did not write (s or t when they are not adjacent: their
+    // W_1 entries are zero, and the block holds no zeros there)
+    auto upd = [&](int32_t u, bool w_zero) {
+        const int64_t e = (int64_t)u * ld + p;
+        a.w[e] = lanczos_next<T>(w_zero ? T(0) : a.w[e], al, a.q1[e], c, ib);
+        atomicOr(a.mask + (e >> 5), 1u << (e & 31));
     };
     const int64_t ds_n = a.row_ptr[s + 1] - a.row_ptr[s], dt_n = a.row_ptr[t + 1] - a.row_ptr[t];
     const int32_t L = ds_n >= dt_n ? s : t, S = ds_n >= dt_n ? t : s;
@@ -712,25 +717,69 @@ __global__ void __launch_bounds__(256) k_normalize_step0(const Step0NormArgs<T> 
         }
         return lo < le && __ldg(a.col + lo) == u;
     };
-    for (int64_t e = lb + threadIdx.x; e < le; e += blockDim.x) upd(__ldg(a.col + e));
+    for (int64_t e = lb + threadIdx.x; e < le; e += blockDim.x) upd(__ldg(a.col + e), false);
     for (int64_t e = sb + threadIdx.x; e < se; e += blockDim.x) {
         const int32_t u = __ldg(a.col + e);
-        if (!in_row_L(u)) upd(u);
+        if (!in_row_L(u)) upd(u, false);
     }
     if (threadIdx.x == 0 && !in_row_L(S)) {
-        upd(s);
-        upd(t);
+        upd(s, true);
+        upd(t, true);
+    }
+}
+
+// Second part: every entry the first part did not mark gets (0 - alpha_1 * 0 - c_1) / beta_2
+// formed as k_normalize forms it from the zeros of W_1 and q_1 there, without reading the
+// block (it holds no zeros there: the sparse first step leaves it unwritten). 16-byte units;
+// a unit with marked entries is written element by element around them.
+template <typename T>
+__global__ void __launch_bounds__(256) k_normalize_step0_fill(const Step0NormArgs<T> a)
+{
+    constexpr int V = 16 / (int)sizeof(T);
+    const int64_t ld = a.ld;
+    const int64_t units = a.n * ld / V;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const T* cf_al = a.cf + ld;
+    const T* cf_c = a.cf + 2 * ld;
+    const T* cf_ib = a.cf + 3 * ld;
+    for (int64_t un = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; un < units; un += stride) {
+        const int64_t e0 = un * V;
+        const int64_t c0 = e0 % ld;
+        const uint32_t bits = (a.mask[e0 >> 5] >> (e0 & 31)) & ((1u << V) - 1u);
+        T al[V], c[V], ib[V], v[V];
+        ld_plain<T, V>(al, cf_al + c0);
+        ld_plain<T, V>(c, cf_c + c0);
+        ld_plain<T, V>(ib, cf_ib + c0);
+#pragma unroll
+        for (int i = 0; i < V; ++i) v[i] = lanczos_next<T>(T(0), al[i], T(0), c[i], ib[i]);
+        if (bits == 0) {
+            st_plain<T, V>(a.w + e0, v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+                if (!((bits >> i) & 1u)) a.w[e0 + i] = v[i];
+        }
     }
 }
 
 template <typename T>
-static void launch_norm0(cudaStream_t st, const Step0NormArgs<T>& a)
+static void launch_norm0(int grid, cudaStream_t st, const Step0NormArgs<T>& a)
 {
     if (a.npairs > 0) k_normalize_step0<T><<<a.npairs, 256, 0, st>>>(a);
+    k_normalize_step0_fill<T><<<grid, 256, 0, st>>>(a);
 }
-void launch_normalize_step0_f32(cudaStream_t st, const Step0NormArgs<float>& a) { launch_norm0<float>(st, a); }
-void launch_normalize_step0_f64(cudaStream_t st, const Step0NormArgs<double>& a) { launch_norm0<double>(st, a); }
-void launch_normalize_step0_df64(cudaStream_t st, const Step0NormArgs<df64>& a) { launch_norm0<df64>(st, a); }
+void launch_normalize_step0_f32(int grid, cudaStream_t st, const Step0NormArgs<float>& a)
+{
+    launch_norm0<float>(grid, st, a);
+}
+void launch_normalize_step0_f64(int grid, cudaStream_t st, const Step0NormArgs<double>& a)
+{
+    launch_norm0<double>(grid, st, a);
+}
+void launch_normalize_step0_df64(int grid, cudaStream_t st, const Step0NormArgs<df64>& a)
+{
+    launch_norm0<df64>(grid, st, a);
+}
 
 void launch_step0_f32(cudaStream_t st, const Step0Args<float>& a) { launch_step0<float>(st, a); }
 void launch_step0_f64(cudaStream_t st, const Step0Args<double>& a) { launch_step0<double>(st, a); }

@@ -53,8 +53,6 @@ SMALL = [
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
 @pytest.mark.parametrize("kernel", ["group", "group_sorted", "stream", "async", "onchip"])
 def test_small_graphs_vs_dense(rd, name, make, mode, kernel):
-    if kernel == "async" and mode == "fp64":
-        pytest.skip("the async row-stream kernel is FP32-vector only")
     g = make()
     s, t = F.random_pairs(g.n, 9, 17)
     ref = dense.DenseRD.of(g).r(s, t)
@@ -437,6 +435,34 @@ def test_compaction_matches_fixed_layout(rd, mode):
     c = G.query(s, t, device_loop=False, **kw)
     assert np.array_equal(c.r, a.r) and np.array_equal(c.iters, a.iters)
     assert G.last_stats()["compactions"] >= st["compactions"]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "df64"])
+def test_async_kernel_8byte_elements(rd, mode):
+    """The async row-stream SpMM with two 8-byte elements per 16-byte lane slot (FP64, or
+    double-float as hi/lo pairs): on a weighted power-law graph with heavy rows and on a
+    weighted road-like grid, every slab width agrees with the oracle at convergence, with the
+    row-group kernel at fixed k, and with itself bitwise on a repeat."""
+    cl, s_cl, t_cl = W.chunglu(20000, 2.1, 20.0, 200000, 37, 77, weights="lognormal")
+    assert np.diff(cl.row_ptr).max() > 256  # heavy rows present
+    gd = F.grid_deleted(48, 0.05, 5)
+    gd = F.weighted(gd, F.lognormal_edge_weights(gd.m, 0.0, 0.5, 6))
+    s_g, t_g = F.random_pairs(gd.n, 21, 8)
+    for g, s, t, k_max in ((cl, s_cl, t_cl, 300), (gd, s_g, t_g, 3000)):
+        G = rd.Graph.from_csr(g)
+        ref, _, _ = lanczos.lanczos_batch(g, s, t, k_max=k_max, stop_tol=1e-15, threads=0)
+        for tile in [16, 32, 64]:
+            kw = dict(mode=mode, kernel="async", rhs_tile=tile, compact=False)
+            res = G.query(s, t, k_max=k_max, rel_tol=0.0, resid_tol=1e-11, **kw)
+            st = G.last_stats()
+            assert st["kernel"] == 5 and st["rhs_tile"] == tile
+            assert np.all(res.status >= 0)
+            assert rel(res.r, ref).max() < FP64_TOL, (tile, rel(res.r, ref).max())
+            fa = G.query(s, t, k_max=20, fixed_k=True, **kw)
+            fg = G.query(s, t, mode=mode, kernel="group", rhs_tile=tile, compact=False, k_max=20, fixed_k=True)
+            assert rel(fa.r, fg.r).max() < 1e-11, (tile, rel(fa.r, fg.r).max())
+            assert np.array_equal(G.query(s, t, k_max=20, fixed_k=True, **kw).r, fa.r)
+        G.close()
 
 
 def test_async_kernel_scattered_heavy_rows(rd):
