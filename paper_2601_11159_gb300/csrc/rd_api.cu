@@ -880,8 +880,9 @@ static void enqueue_init(RunCtx& c, bool replay)
 // at least `active_upper` slots, an upper bound on the active count read one step ago).
 // With fuse_step >= 0 the packing is fused with that step's normalise pass (its SpMM and
 // finalize have run: q[0] holds W and q[1] holds q_j): k_normalize_pack writes q_{j+1} and
-// q_j packed, and *fused reports whether it ran (the caller then runs the plain pass when it
-// did not: no narrower layout, or no whole 16-byte units).
+// q_j packed, and *fused reports whether it ran. When it did not (no narrower layout, or one
+// without whole 16-byte units, such as the single-column layout of the last active pair),
+// the caller runs the plain pass and then the packing without fusion.
 template <typename T>
 static rd_status enqueue_compaction(RunCtx& c, int active_upper, int fuse_step = -1, bool* fused = nullptr)
 {
@@ -1261,9 +1262,10 @@ static rd_status run_forward(RunCtx& c)
                     c.spmm_bytes += bytes_per_step;
                     bool fused = false;
                     RD_TRY(enqueue_compaction<T>(c, act_lag, jn, &fused));
-                    if (!fused) {
+                    if (!fused) {  // the plain pass, then the packing if there is one to make
                         enqueue_normalize<T>(c, jn, false);
                         std::swap(c.b.q[0], c.b.q[1]);
+                        RD_TRY(enqueue_compaction<T>(c, act_lag));
                     }
                     launch_step_advance(c.st, c.b.step_dev, c.pl.k_max);
                     ++c.launches;

@@ -730,28 +730,27 @@ __global__ void __launch_bounds__(256) k_normalize_step0(const Step0NormArgs<T> 
 
 // Second part: every entry the first part did not mark gets (0 - alpha_1 * 0 - c_1) / beta_2
 // formed as k_normalize forms it from the zeros of W_1 and q_1 there, without reading the
-// block (it holds no zeros there: the sparse first step leaves it unwritten). 16-byte units;
-// a unit with marked entries is written element by element around them.
+// block (it holds no zeros there: the sparse first step leaves it unwritten). Thread t keeps
+// one 16-byte column unit (its values in registers) and walks the rows t / units,
+// + rows_per_pass, ...; a unit with marked entries is written element by element around them.
 template <typename T>
 __global__ void __launch_bounds__(256) k_normalize_step0_fill(const Step0NormArgs<T> a)
 {
     constexpr int V = 16 / (int)sizeof(T);
     const int64_t ld = a.ld;
-    const int64_t units = a.n * ld / V;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const T* cf_al = a.cf + ld;
-    const T* cf_c = a.cf + 2 * ld;
-    const T* cf_ib = a.cf + 3 * ld;
-    for (int64_t un = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; un < units; un += stride) {
-        const int64_t e0 = un * V;
-        const int64_t c0 = e0 % ld;
-        const uint32_t bits = (a.mask[e0 >> 5] >> (e0 & 31)) & ((1u << V) - 1u);
-        T al[V], c[V], ib[V], v[V];
-        ld_plain<T, V>(al, cf_al + c0);
-        ld_plain<T, V>(c, cf_c + c0);
-        ld_plain<T, V>(ib, cf_ib + c0);
+    const int64_t units = ld / V;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t rows_per_pass = (int64_t)gridDim.x * blockDim.x / units;
+    const int64_t r0 = t / units;
+    if (r0 >= rows_per_pass) return;
+    const int64_t c0 = (t % units) * V;
+    T v[V];
 #pragma unroll
-        for (int i = 0; i < V; ++i) v[i] = lanczos_next<T>(T(0), al[i], T(0), c[i], ib[i]);
+    for (int i = 0; i < V; ++i)
+        v[i] = lanczos_next<T>(T(0), a.cf[ld + c0 + i], T(0), a.cf[2 * ld + c0 + i], a.cf[3 * ld + c0 + i]);
+    for (int64_t u = r0; u < a.n; u += rows_per_pass) {
+        const int64_t e0 = u * ld + c0;
+        const uint32_t bits = (a.mask[e0 >> 5] >> (e0 & 31)) & ((1u << V) - 1u);
         if (bits == 0) {
             st_plain<T, V>(a.w + e0, v);
         } else {
@@ -766,7 +765,10 @@ template <typename T>
 static void launch_norm0(int grid, cudaStream_t st, const Step0NormArgs<T>& a)
 {
     if (a.npairs > 0) k_normalize_step0<T><<<a.npairs, 256, 0, st>>>(a);
-    k_normalize_step0_fill<T><<<grid, 256, 0, st>>>(a);
+    // at least one row per pass (the host takes this path only for whole 16-byte units)
+    const int64_t units = a.ld / (16 / (int64_t)sizeof(T));
+    const int g = (int)std::max<int64_t>(grid, (units + 255) / 256);
+    k_normalize_step0_fill<T><<<g, 256, 0, st>>>(a);
 }
 void launch_normalize_step0_f32(int grid, cudaStream_t st, const Step0NormArgs<float>& a)
 {

@@ -152,6 +152,16 @@ def test_chunglu4m_weighted_gradient(rd):
     r64 = G.query(s, t, mode="fp64", k_max=200, rel_tol=0.0, resid_tol=1e-12).r
     assert rel(r32[idx], ref).max() < FP32_TOL
     assert rel(r64[idx], ref).max() < FP64_TOL
+    # the device-resident loop packs the columns where the host polls do: a step here moves
+    # more than 1.5 GB, so both read the current active count, and the last packing leaves
+    # one active pair (a one-column layout, which the fused normalise-and-pack cannot take)
+    a = G.query(s, t, mode="fp32", k_max=200, rel_tol=1e-6)
+    sa = G.last_stats()
+    b = G.query(s, t, mode="fp32", k_max=200, rel_tol=1e-6, device_loop=False)
+    sb = G.last_stats()
+    assert sa["device_loop"] == 1 and sb["device_loop"] == 0
+    assert np.array_equal(a.r, b.r) and np.array_equal(a.iters, b.iters)
+    assert sa["compactions"] == sb["compactions"] >= 1, (sa["compactions"], sb["compactions"])
 
     # (i) one-hot upstream gradient on pair 0 vs the oracle potential of pair 0
     onehot = np.zeros(s.size)
