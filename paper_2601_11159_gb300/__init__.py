@@ -106,6 +106,15 @@ def _opts(k_max=1000, rel_tol=1e-7, resid_tol=0.0, mode="fp32", rhs_tile=0, rows
           fixed_k=False, deflate=True, plain=False, profile=False, kernel=0, compact=True,
           onchip=True, tune=True, graph=True, estimate="geometric", sparse_first=True,
           potential_mode="direct", cluster=True, device_loop=True) -> _lib.QueryOpts:
+    """rd_query_opts from keywords (each documented in include/rd.h): k_max, rel_tol,
+    resid_tol, mode ("fp32" FP32 vectors with FP64 scalars, "fp64", "df64"), rhs_tile,
+    rows_per_warp, chunk_steps, kernel ("tuned", "group", "stream", "group_sorted", "tasks",
+    "async" or its number); the booleans clear or set one flag each: fixed_k (RD_Q_FIXED_K),
+    deflate (RD_Q_NO_DEFLATE), plain (RD_Q_PLAIN), profile (RD_Q_PROFILE), compact
+    (RD_Q_NO_COMPACT), onchip (RD_Q_NO_ONCHIP), tune (RD_Q_NO_TUNE), graph (RD_Q_NO_GRAPH),
+    sparse_first (RD_Q_DENSE_FIRST), cluster (RD_Q_NO_CLUSTER), device_loop
+    (RD_Q_NO_DEVICE_LOOP); estimate "geometric" or "delayed" (RD_Q_EST_DELAYED);
+    potential_mode "direct" or "replay" (RD_Q_REPLAY_POTENTIAL)."""
     o = _lib.QueryOpts()
     lib().rd_query_opts_init(C.byref(o))
     o.k_max = int(k_max)
