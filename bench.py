@@ -269,11 +269,13 @@ def profile_config(rd, name, call="query"):
     from graphgen import workloads as W
 
     make = {"chunglu1m": W.chunglu1m, "rmat24": W.rmat24, "roadgrid4096": W.roadgrid4096,
-            "chunglu4m_w": W.chunglu4m_w, "grid64": W.grid64}[name]
+            "chunglu4m_w": W.chunglu4m_w, "grid64": W.grid64,
+            # a small road grid (1024^2, 64 pairs at distance 256) for multi-pass ncu captures
+            "roadgrid1024": lambda: W.roadgrid(1024, 64, 256)}[name]
     g, s, t = make()
     G = rd.Graph.from_csr(g)
     sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
-    mode = "df64" if name == "roadgrid4096" else "fp32"
+    mode = "df64" if name.startswith("roadgrid") else "fp32"
     if name == "grid64":  # the single-pair latency workload as the bench line runs it
         mode = "fp64"
         kw = dict(mode=mode, k_max=500, rel_tol=0.0, resid_tol=1e-10)
@@ -561,8 +563,9 @@ def main():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--only", default=None,
-                    choices=["grid64", "chunglu1m", "rmat24", "roadgrid4096", "chunglu4m_w"],
-                    help="with --sweep configs: one workload; with --profile-range: a short profiled query of it")
+                    choices=["grid64", "chunglu1m", "rmat24", "roadgrid4096", "chunglu4m_w", "roadgrid1024"],
+                    help="with --sweep configs: one workload; with --profile-range: a short profiled query of it "
+                         "(roadgrid1024: profiling only)")
     ap.add_argument("--profile-call", default="query", choices=["query", "grad"],
                     help="with --sweep configs --profile-range: the profiled call (grad: rd_edge_grad)")
     ap.add_argument("--sweep", default=None, choices=["scaling", "density", "pm", "configs", "kappa", "all"],
