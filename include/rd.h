@@ -124,8 +124,10 @@ typedef enum {
                                the active count between steps. By default the steps after the first
                                run in one graph whose conditional (while) node repeats the step on
                                the device until every pair has stopped, k_max is reached or a column
-                               compaction is due; the host steps in only to pack the columns. Both
-                               give bitwise the same results */
+                               compaction is due; the host steps in only to pack the columns, with
+                               the normalise pass of the step before the packing fused into it. Both
+                               give bitwise the same results (the device loop may skip a packing
+                               that the host-driven loop makes after the last pair has stopped) */
 
 typedef struct {
     int32_t k_max;         /* step cap (>= 1) */
