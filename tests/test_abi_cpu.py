@@ -126,6 +126,8 @@ def test_header_constants_match_the_binding():
     assert rd._opts(potential_mode="replay").flags == _lib.RD_Q_REPLAY_POTENTIAL
     assert rd._opts(graph=False, tune=False).flags == _lib.RD_Q_NO_GRAPH | _lib.RD_Q_NO_TUNE
     assert rd._opts(estimate="delayed").flags == _lib.RD_Q_EST_DELAYED
+    assert rd._opts(cluster=False).flags == _lib.RD_Q_NO_CLUSTER
+    assert rd._opts(device_loop=False).flags == _lib.RD_Q_NO_DEVICE_LOOP
     with pytest.raises(ValueError):
         rd._opts(potential_mode="stored")
     with pytest.raises(ValueError):
